@@ -1,0 +1,252 @@
+"""FP64 CPU oracle for the periodic lattice Boltzmann scheme for linear elasticity
+(Boolakee, Geier, De Lorenzis, arXiv 2208.14870).
+
+TEST INFRASTRUCTURE ONLY.  The oracle exists to check the CUDA library; only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It shares no code with the CUDA path and never
+imports the library package.
+
+Parts:
+  * ``lbm_oracle.c`` (loaded here through ctypes): Algorithm 1 written out
+    node by node in plain C, FP64 -- moments (Eq. moments, Eq. replace_raw),
+    half forcing (Eqs. coll10/coll01 and coll10post/coll01post), Table 1
+    equilibria, relaxation (Eq. collision), back-transformation
+    (Eq. moments_post), streaming (Eq. streaming) with the periodic wrap of
+    Sec. 5.1, and the solution fields of Table 2.
+  * this module: the relaxation rates tied to the Lame parameters (Table 1,
+    Eqs. match11/matchd/matchs, Eq. relaxation_rate), the 2D material
+    relations (Eq. material_relations), the pseudo-time loop to steady state
+    (Sec. 2.1: iterate until the change of u is below a tolerance) and the
+    grid norms of Sec. 6.1.
+  * ``fourier.py``: the one-step operator of Eq. lbmvector, its von Neumann
+    spectral radius (Sec. 4), and the exact discrete steady state mode by
+    mode.
+
+Every function here is pinned by ``tests/test_oracle_*.py`` against the
+paper's printed values, closed forms, brute force on small lattices and exact
+invariants.  No function is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD_DIR, "liblbm_oracle.so")
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+THETA_STANDARD = 1.0 / 3.0  # Sec. 3.3.2 (isotropy argument), Table 1
+
+
+def build(force: bool = False) -> str:
+    """Compile ``lbm_oracle.c`` into ``oracle/_build/liblbm_oracle.so`` (gcc, -O2,
+    no FMA contraction).  Returns the path of the shared object."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call([
+            "gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99",
+            "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                       dp, ctypes.c_long, dp, dp]
+            lib.oracle_collide.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
+                                           dp, dp, dp]
+            lib.oracle_moments.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+            lib.oracle_fields.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                          dp, dp]
+            lib.oracle_raw_moment_inverse.argtypes = [ctypes.c_int, dp]
+            for fn in (lib.oracle_run, lib.oracle_collide, lib.oracle_moments,
+                       lib.oracle_fields, lib.oracle_raw_moment_inverse):
+                fn.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ----------------------------------------------------------------------------
+# Material parameters and relaxation rates
+# ----------------------------------------------------------------------------
+
+def lame_2d(E: float, nu: float) -> tuple[float, float]:
+    """Lame parameters of the 2D (not plane-strain) medium, Eq. material_relations:
+    lambda = E nu / (1 - nu^2), mu = E / (2 (1 + nu))."""
+    return E * nu / (1.0 - nu * nu), E / (2.0 * (1.0 + nu))
+
+
+def relaxation_rates(lam: float, mu: float, theta: float = THETA_STANDARD,
+                     tau12: float = 0.5, tau22: float = 0.5) -> np.ndarray:
+    """Rates [w_11, w_s, w_d, w_12, w_21, w_22, theta] in lattice units.
+
+    Table 1 / Eqs. match11, matchd, matchs: theta*tau_11 = mu,
+    (1 - theta)/2 * tau_d = mu, (1 + theta)/2 * tau_s = K with K = lambda + mu
+    (Eq. material_relations); tau_12 = tau_21 and tau_22 default to 1/2
+    (Sec. 3.3.2, last remarks).  Eq. relaxation_rate: w = 1 / (tau + 1/2).
+    """
+    K = lam + mu
+    tau11 = mu / theta
+    tau_d = 2.0 * mu / (1.0 - theta)
+    tau_s = 2.0 * K / (1.0 + theta)
+    w = [1.0 / (t + 0.5) for t in (tau11, tau_s, tau_d, tau12, tau12, tau22)]
+    return np.array(w + [theta], dtype=np.float64)
+
+
+def fourth_order_taus(lam: float, mu: float, theta: float = THETA_STANDARD) -> tuple[float, float]:
+    """tau_12 = tau_21 and tau_22 of the fourth-order special case (Appendix C)."""
+    K = lam + mu
+    t11 = mu / theta
+    td = 2.0 * mu / (1.0 - theta)
+    ts = 2.0 * K / (1.0 + theta)
+    tau12 = (2.0 - 3.0 * theta + 12.0 * theta * t11 ** 2) / (12.0 * (1.0 - theta) * t11)
+    num = ((1.0 - theta) * td + (1.0 + theta) * ts) * (
+        theta * (2.0 - 3.0 * theta) * (ts - td) - 12.0 * theta ** 2 * t11 ** 2 * (ts - td)
+        + 2.0 * t11 * (1.0 - theta - 6.0 * (1.0 - theta) ** 2 * td ** 2
+                       - 6.0 * (1.0 - theta ** 2) * ts ** 2))
+    den = 2.0 * theta * (2.0 - 3.0 * theta + 12.0 * theta * t11 ** 2) * (ts - td)
+    return tau12, num / den
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 1 through the C oracle
+# ----------------------------------------------------------------------------
+
+def zero_state(nx: int, ny: int, q: int = 8) -> np.ndarray:
+    """Initial populations at the equilibrium of u_0 = 0, i.e. all zero
+    (Eq. init_cond with Table 1)."""
+    return np.zeros((q, ny, nx), dtype=np.float64)
+
+
+def run(f: np.ndarray, gx: np.ndarray, gy: np.ndarray, rates: np.ndarray,
+        nsteps: int = 1) -> np.ndarray:
+    """Advance pre-collision populations f[q, ny, nx] by ``nsteps`` steps of
+    Algorithm 1; returns a new array."""
+    q, ny, nx = f.shape
+    fin = np.ascontiguousarray(f, dtype=np.float64)
+    gx = np.ascontiguousarray(gx, dtype=np.float64)
+    gy = np.ascontiguousarray(gy, dtype=np.float64)
+    w = np.ascontiguousarray(rates, dtype=np.float64)
+    assert gx.shape == (ny, nx) and gy.shape == (ny, nx) and w.shape == (7,)
+    out = np.empty_like(fin)
+    tmp = np.empty_like(fin)
+    rc = _load().oracle_run(nx, ny, q, _ptr(fin), _ptr(gx), _ptr(gy), _ptr(w), int(nsteps),
+                            _ptr(out), _ptr(tmp))
+    if rc != 0:
+        raise ValueError("oracle_run rejected its arguments")
+    return out
+
+
+def collide(f: np.ndarray, gx: np.ndarray, gy: np.ndarray, rates: np.ndarray) -> np.ndarray:
+    """Post-collision populations f* (collision stage of Algorithm 1 only)."""
+    q, ny, nx = f.shape
+    fin = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(fin)
+    rc = _load().oracle_collide(nx, ny, q, _ptr(fin), _ptr(np.ascontiguousarray(gx, np.float64)),
+                                _ptr(np.ascontiguousarray(gy, np.float64)),
+                                _ptr(np.ascontiguousarray(rates, np.float64)), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_collide rejected its arguments")
+    return out
+
+
+def moments(f: np.ndarray) -> np.ndarray:
+    """Collision-basis moments [m_10, m_01, m_11, m_s, m_d, m_12, m_21, m_22(, m_00)]."""
+    q, ny, nx = f.shape
+    fin = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(fin)
+    if _load().oracle_moments(nx, ny, q, _ptr(fin), _ptr(out)) != 0:
+        raise ValueError("oracle_moments rejected its arguments")
+    return out
+
+
+def fields(f: np.ndarray, gx: np.ndarray, gy: np.ndarray, rates: np.ndarray) -> np.ndarray:
+    """Solution fields [u_x, u_y, sigma_xx, sigma_yy, sigma_xy] (lattice units)
+    of the pre-collision state f (Table 2, Eq. compute_bared)."""
+    q, ny, nx = f.shape
+    fin = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty((5, ny, nx), dtype=np.float64)
+    rc = _load().oracle_fields(nx, ny, q, _ptr(fin), _ptr(np.ascontiguousarray(gx, np.float64)),
+                               _ptr(np.ascontiguousarray(gy, np.float64)),
+                               _ptr(np.ascontiguousarray(rates, np.float64)), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_fields rejected its arguments")
+    return out
+
+
+def raw_moment_inverse(q: int = 8) -> np.ndarray:
+    out = np.empty((q, q), dtype=np.float64)
+    if _load().oracle_raw_moment_inverse(q, _ptr(out)) != 0:
+        raise ValueError("bad q")
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Pseudo-time iteration to steady state (Sec. 2.1) and grid norms (Sec. 6.1)
+# ----------------------------------------------------------------------------
+
+def residual(u_now: np.ndarray, u_prev: np.ndarray, k: int) -> tuple[float, float]:
+    """Steady-state residual over a window of k steps.
+
+    The paper stops when the time derivative of u is below a tolerance "in
+    some norm" (Sec. 2.1).  Reading: r_inf = max|u^n - u^{n-k}| /
+    (k * max|u^n|) with max over nodes and components, and the L2 analogue
+    r_2 = ||u^n - u^{n-k}||_2 / (k * ||u^n||_2); r = 0 when u^n = 0.
+    """
+    d = u_now - u_prev
+    umax = float(np.max(np.abs(u_now))) if u_now.size else 0.0
+    u2 = float(np.sqrt(np.sum(u_now * u_now)))
+    dmax = float(np.max(np.abs(d))) if d.size else 0.0
+    d2 = float(np.sqrt(np.sum(d * d)))
+    r_inf = 0.0 if umax == 0.0 else dmax / (k * umax)
+    r_2 = 0.0 if u2 == 0.0 else d2 / (k * u2)
+    return r_inf, r_2
+
+
+def solve(gx: np.ndarray, gy: np.ndarray, rates: np.ndarray, tol: float,
+          check_every: int = 100, max_iters: int = 10_000_000, q: int = 8,
+          f0: np.ndarray | None = None):
+    """Iterate Algorithm 1 from the zero state until the residual
+    (``residual``) drops below ``tol``.  Returns (f, iters, r_inf)."""
+    ny, nx = gx.shape
+    f = zero_state(nx, ny, q) if f0 is None else f0
+    u_prev = fields(f, gx, gy, rates)[:2]
+    it = 0
+    r = float("inf")
+    while it < max_iters:
+        f = run(f, gx, gy, rates, check_every)
+        it += check_every
+        u = fields(f, gx, gy, rates)[:2]
+        r, _ = residual(u, u_prev, check_every)
+        if not np.all(np.isfinite(u)):
+            raise FloatingPointError("oracle diverged at step %d" % it)
+        if r < tol:
+            break
+        u_prev = u
+    return f, it, r
+
+
+def grid_norms(err: np.ndarray, dx: float) -> tuple[float, float]:
+    """L2 and Linf grid norms of a vector field err[c, ny, nx] (Sec. 6.1):
+    L2 = (dx^2 sum_i |e_i|_2^2)^(1/2), Linf = max_i |e_i|_inf."""
+    l2 = float(np.sqrt(dx * dx * np.sum(err * err)))
+    linf = float(np.max(np.abs(err)))
+    return l2, linf
