@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 lattice Boltzmann elasticity solver.
+
+Workload (default): the single-large-lattice throughput case -- a 16384 x 16384
+doubly periodic lattice, FP32 population storage, E~ = 1, nu = 0.3, body force
+made of 16 seeded random Fourier modes (amplitudes N(0,1)/|k|^2, |k_x|, |k_y| <= 8).
+One benchmark step is one pass of the whole hot path over that input: reset to
+the zero state, 1000 fixed pseudo-time steps of the fused stream-collide kernel
+with the fused steady-state residual every 100 steps, then the FP64
+displacement / stress recovery.  The metric is MLUPS (million lattice-node
+updates per second); the stream-collide kernel's achieved HBM bandwidth is
+reported against the measured copy peak.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica on its own GPU (the
+problem does not shard; replicas only).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "MLUPS and HBM GB/s (% of GB300 peak); solves/sec and p99 latency, batched vs plain"
+FALLBACK_HBM_GBS = 6800.0
+# Algorithmic bytes per lattice update (one node, one step): 8 populations
+# read + 8 written + 2 force components read; FP16-shifted adds the two FP32
+# first-moment carriers read and written.
+BYTES_PER_LUP = {"f64": 8 * 8 * 2 + 2 * 8, "f32": 8 * 4 * 2 + 2 * 4, "f16s": (8 * 2 + 2 * 4) * 2 + 2 * 4}
+FORCE_SEED = 0x2208_14870
+# DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype,
+# with the hash of the kernel sources it was taken on (null once they change).
+NCU_TRAFFIC = {}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbm_core.cuh", "lbm_kernels.cuh", "lbm_ops.cuh"):
+        with open(os.path.join(ROOT, "paper_2208_14870_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax = float(row[2])
+                power.append(float(row[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_force(n: int):
+    pw = W.random_force(n, n, n_modes=16, kmax=8, seed=FORCE_SEED)
+    return W.random_force_grid(pw)
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    lam, mu = W.lame_2d(1.0, args.nu)
+    rates = oracle.relaxation_rates(lam, mu)
+    m = args.ref_n
+    pw = W.random_force(m, m, n_modes=16, kmax=8, seed=FORCE_SEED)
+    gx, gy = W.random_force_grid(pw)
+    f = oracle.zero_state(m, m)
+    iters = args.ref_iters
+    for _ in range(args.warmup):
+        oracle.run(f, gx, gy, rates, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.run(oracle.zero_state(m, m), gx, gy, rates, iters)
+        oracle.fields(f, gx, gy, rates)
+    dt = time.perf_counter() - t0
+    mlups = m * m * iters * args.steps / dt / 1e6
+    sample = ("%dx%d lattice, same 16-mode force recipe, %d pseudo-time steps + field recovery "
+              "per benchmark step (oracle, single thread)" % (m, m, iters))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args),
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": "single large lattice throughput: %dx%d periodic D2Q8, %s storage, "
+                        "16 random Fourier force modes, %d fixed steps/step" % (
+                            args.n, args.n, args.dtype.upper(), args.iters),
+            "nx": args.n, "ny": args.n, "iters_per_step": args.iters,
+            "check_every": args.check_every, "E": 1.0, "nu": args.nu,
+            "force": "16 modes, |kx|,|ky|<=8, amp N(0,1)/|k|^2, seed %#x" % FORCE_SEED,
+            "l2": "inputs larger than L2 (population state %.1f GB)" % (
+                args.n * args.n * BYTES_PER_LUP[args.dtype] / 1e9)}
+
+
+def cpu_baseline(args):
+    import oracle
+    oracle.build()
+    lam, mu = W.lame_2d(1.0, args.nu)
+    rates = oracle.relaxation_rates(lam, mu)
+    m, it = args.ref_n, args.ref_iters
+    pw = W.random_force(m, m, n_modes=16, kmax=8, seed=FORCE_SEED)
+    gx, gy = W.random_force_grid(pw)
+    t0 = time.perf_counter()
+    oracle.run(oracle.zero_state(m, m), gx, gy, rates, it)
+    dt = time.perf_counter() - t0
+    return {"value": m * m * it / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%dx%d lattice, same force recipe, %d steps, single-threaded FP64 C oracle "
+                      "(%.1f s)" % (m, m, it, dt)}
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True):
+    """Device-resident timing of `nsteps` benchmark steps; returns dict."""
+    n = args.n
+    lam, mu = W.lame_2d(1.0, args.nu)
+    lat = P.Lattice(n, n, lam, mu, dtype)
+    stream = torch.cuda.current_stream()
+    lat.set_stream(stream.cuda_stream)
+    lat.set_force(gx_d, gy_d)
+    out5 = torch.empty(5 * n * n, dtype=torch.float64, device="cuda")
+
+    def one_step(ev_a=None, ev_b=None):
+        lat.reset()
+        if ev_a is not None:
+            ev_a.record(stream)
+        P.lbm_iterate_checked(lat.ctx, args.iters, args.check_every, None)
+        if ev_b is not None:
+            ev_b.record(stream)
+        lat.fields_device(out5)
+
+    for _ in range(nwarm):
+        one_step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(nsteps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for a, b in evs:
+        one_step(a, b)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    total_ms = t_start.elapsed_time(t_end)
+    iter_ms = sum(a.elapsed_time(b) for a, b in evs)
+    lat.close()
+    del out5
+    return {"total_ms": total_ms, "iter_ms": iter_ms, "steps": nsteps,
+            "launches": nsteps * (args.iters + 1)}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2208_14870_gb300 as P
+
+    n = args.n
+    gx, gy = make_force(n)
+    gx_d = torch.from_numpy(gx).cuda()
+    gy_d = torch.from_numpy(gy).cuda()
+    peak, peak_kind = measured_peaks()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local if ws > 1 else torch.cuda.current_device())
+    barrier()
+    sampler.start()
+    res = time_variant(args, args.dtype, gx_d, gy_d, torch, P, args.steps, args.warmup)
+    barrier()
+    clocks = sampler.stop()
+    t = torch.tensor([res["total_ms"]], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    lups = float(n) * n * args.iters * args.steps * ws
+    value = lups / (total_ms / 1e3) / 1e6
+    per_launch_s = res["iter_ms"] / 1e3 / (args.steps * args.iters)
+    bpl = BYTES_PER_LUP[args.dtype] * n * n
+    achieved = bpl / per_launch_s / 1e9
+    tr = NCU_TRAFFIC.get(args.dtype)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_hash") == kernel_hash() else None
+
+    variants = {}
+    if not args.quick:
+        for dt in args.variants:
+            if dt == args.dtype:
+                continue
+            r = time_variant(args, dt, gx_d, gy_d, torch, P, max(2, args.steps // 2), 2)
+            pl = r["iter_ms"] / 1e3 / (r["steps"] * args.iters)
+            variants[dt] = {
+                "value": float(n) * n * args.iters * r["steps"] / (r["total_ms"] / 1e3) / 1e6,
+                "unit": "MLUPS", "ms_per_step": r["total_ms"] / r["steps"],
+                "kernel_us": pl * 1e6,
+                "achieved_gbs": BYTES_PER_LUP[dt] * n * n / pl / 1e9,
+                "frac_of_measured_hbm": BYTES_PER_LUP[dt] * n * n / pl / 1e9 / peak,
+                "bytes_per_lup": BYTES_PER_LUP[dt]}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, gx, gy, torch, P, ws, dist if ws > 1 else None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+            "data": "synthetic (seeded random Fourier-mode body force)",
+            "config": workload_config(args),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_step<%s> (fused stream-collide)" % args.dtype,
+                         "kernel_us": per_launch_s * 1e6,
+                         "bytes_per_lup": BYTES_PER_LUP[args.dtype],
+                         "peak_kind": peak_kind + " copy bandwidth",
+                         "frac_of_nominal_8tbs": achieved / 8000.0},
+            "clocks": clocks,
+            "gpu_launches": res["launches"],
+            "e2e": e2e,
+            "variants": variants,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, gx, gy, torch, P, ws, dist):
+    """Through the public API with host buffers: upload the force from pinned
+    host memory, reset, iterate with residual checks, read displacement and
+    stress back into pinned host memory -- every step."""
+    n = args.n
+    lam, mu = W.lame_2d(1.0, args.nu)
+    lat = P.Lattice(n, n, lam, mu, args.dtype)
+    hgx = torch.from_numpy(gx).pin_memory()
+    hgy = torch.from_numpy(gy).pin_memory()
+    outs = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(5)]
+    res = np.zeros(5)
+
+    def step():
+        P.lbm_set_force(lat.ctx, hgx.data_ptr(), hgy.data_ptr())
+        P.lbm_reset(lat.ctx)
+        P.lbm_iterate_checked(lat.ctx, args.iters, args.check_every, res.ctypes.data)
+        P.lbm_get_displacement(lat.ctx, outs[0].data_ptr(), outs[1].data_ptr())
+        P.lbm_get_stress(lat.ctx, outs[2].data_ptr(), outs[3].data_ptr(), outs[4].data_ptr())
+
+    for _ in range(args.e2e_warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dt = float(t.item())
+    lat.close()
+    return {"value": float(n) * n * args.iters * args.e2e_steps * ws / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 5 * n * n * 8 + 5 * 8,
+            "steps": args.e2e_steps, "ms_per_step": dt / args.e2e_steps * 1e3,
+            "api": "lbm_set_force(host) + lbm_reset + lbm_iterate_checked + "
+                   "lbm_get_displacement/lbm_get_stress(host)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--iters", type=int, default=1000)
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--dtype", default="f32", choices=["f64", "f32", "f16s"])
+    ap.add_argument("--nu", type=float, default=0.3)
+    ap.add_argument("--variants", nargs="*", default=["f16s"])
+    ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-warmup", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-n", type=int, default=1024)
+    ap.add_argument("--ref-iters", type=int, default=40)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

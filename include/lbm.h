@@ -1,0 +1,192 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the periodic lattice
+ * Boltzmann scheme for quasi-static linear elasticity of Boolakee, Geier and
+ * De Lorenzis, "A new lattice Boltzmann scheme for linear elastic solids:
+ * periodic problems" (arXiv 2208.14870).
+ *
+ * The library advances one D2Q8 distribution function (the D2Q9 set without
+ * its inert rest population, Sec. 3.3.2) on a doubly periodic nx-by-ny
+ * lattice in pseudo-time until the displacement reaches the quasi-static
+ * steady state of the damped Navier-Cauchy equation (Eq. linelasdamp), and
+ * recovers displacement and Cauchy stress from the moments (Table 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Lattice units: Delta x = Delta t = 1.  lambda and mu are the
+ *    dimensionless Lame parameters (Sec. 2.2); K = lambda + mu
+ *    (Eq. material_relations).  The body force g is the lattice force
+ *    g = eps^2 g^(2) of Sec. 3.3.2 (for a problem posed on the unit square
+ *    with E~ = 1, g = b / N^2).
+ *  - Fields are row-major nx*ny arrays: node (x, y), 0 <= x < nx,
+ *    0 <= y < ny, at index y*nx + x; the node sits at ((x+1/2), (y+1/2))
+ *    (Sec. 5.1: the lattice is offset by half a spacing from the periodic
+ *    boundary).
+ *  - Population arrays are 8 planes of nx*ny doubles in the paper's
+ *    one-index order (Sec. 4, population table):
+ *      c = (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+ *    They hold the pre-collision populations f_i(x, t) (input of
+ *    Algorithm 1).
+ *  - Stress is returned in lattice units: sigma_lat = eps * sigma~, i.e.
+ *    sigma_xx = -(mbar_s + mbar_d)/2, sigma_yy = -(mbar_s - mbar_d)/2,
+ *    sigma_xy = -mbar_11 (Table 2 without the 1/eps factor).
+ *  - Host pointers are caller-owned; the library never keeps them after the
+ *    call returns.  Device pointers ("_device" entry points) are CUDA global
+ *    memory of the current device; the caller keeps ownership.
+ *  - Every call returns a status (LBM_OK = 0 or a negative LBM_ERR_*), never
+ *    aborts, and leaves a human-readable message for lbm_last_error().
+ *  - Work is enqueued on the context's stream (lbm_set_stream; default: the
+ *    legacy default stream).  Calls that read or write host buffers, and
+ *    lbm_solve, synchronise that stream before returning; lbm_iterate,
+ *    lbm_reset, lbm_set_force_device and lbm_get_fields_device only enqueue.
+ *  - A context belongs to the device that was current at lbm_create and
+ *    must be used from one host thread at a time.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Population storage type.  Collision arithmetic is FP64 for LBM_F64 and
+ * FP32 for the other two.
+ *  LBM_F64  : 8 FP64 planes.
+ *  LBM_F32  : 8 FP32 planes.
+ *  LBM_F16S : "shifted" FP16 storage: per node the first post-collision
+ *             moments (m*_10, m*_01) in FP32 and, per population, the FP16
+ *             deviation f*_i - E_i from an equilibrium-type part E_i that is
+ *             M^-1 applied to (m*_10, m*_01, 0, 0, 0, theta m*_10,
+ *             theta m*_01, 0); the deviations carry a power-of-two scale
+ *             chosen from the force so they stay in FP16's normal range. */
+enum lbm_dtype { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2 };
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,            /* invalid argument (sizes, moduli, NaN, null pointer) */
+    LBM_ERR_OOM = -2,            /* device or pinned host allocation failed */
+    LBM_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+    LBM_ERR_DIVERGED = -4,       /* non-finite displacement seen by the residual check */
+    LBM_ERR_NOT_CONVERGED = -5,  /* lbm_solve reached max_iters above tolerance */
+    LBM_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
+    LBM_ERR_STATE = -7           /* call not valid in the current state */
+};
+
+/* Optional scheme parameters (lbm_create_ex).  Zero-initialise, then set:
+ *   theta : equilibrium constant of m_12^eq = theta*mbar_10 (Sec. 3.3.2);
+ *           0 means the standard 1/3.  Must lie in (0, 1).
+ *   tau12 : relaxation time of m_12 and m_21 (Eq. relaxation_time);
+ *           0 means the standard 1/2 (rate 1).
+ *   tau22 : relaxation time of m_22; 0 means 1/2.
+ * Non-standard tau12/tau22 reproduce the fourth-order special case of
+ * Sec. 6.3.3 / Appendix C. */
+typedef struct lbm_options {
+    double theta;
+    double tau12;
+    double tau22;
+} lbm_options;
+
+/* Relaxation rates in use (Table 1 with Eq. relaxation_rate:
+ * w = 1/(tau + 1/2), theta tau_11 = mu, (1 - theta)/2 tau_d = mu,
+ * (1 + theta)/2 tau_s = K). */
+typedef struct lbm_rates {
+    double w11, ws, wd, w12, w21, w22, theta;
+} lbm_rates;
+
+/* Create a context: allocates the population buffers (two, ping-pong), the
+ * force, the displacement snapshot of the residual check and the reduction
+ * scratch on the current device, and sets the state to the equilibrium of
+ * u_0 = 0, i.e. all populations zero (Eq. init_cond), with zero force.
+ * nx, ny >= 1; mu > 0; lambda + mu > 0; dtype one of lbm_dtype.
+ * Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_create(int nx, int ny, double lambda, double mu, int dtype, lbm_ctx **out);
+int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype,
+                  const lbm_options *opt, lbm_ctx **out);
+
+/* Free everything the context owns (synchronises its stream first).  Null is
+ * ignored. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Use `stream` (a cudaStream_t, may be null for the legacy default stream) for
+ * all later work of this context.  The caller keeps ownership of the stream. */
+int lbm_set_stream(lbm_ctx *ctx, void *stream);
+
+/* Body force (constant in pseudo-time, Sec. 2.1).  gx, gy: host arrays of
+ * nx*ny doubles (lattice units), copied.  The force must be finite; the
+ * steady state exists for a zero-mean force (the mean of u is conserved,
+ * Sec. 6.2), which is the caller's responsibility.  For LBM_F16S a change of
+ * the force magnitude rescales the stored deviations.  Synchronous. */
+int lbm_set_force(lbm_ctx *ctx, const double *gx, const double *gy);
+
+/* Same, from device arrays of nx*ny doubles.  Enqueued only. */
+int lbm_set_force_device(lbm_ctx *ctx, const double *gx, const double *gy);
+
+/* Back to the zero state (Eq. init_cond with u_0 = 0); step counter 0; the
+ * residual snapshot is invalidated.  The force is kept.  Enqueued only. */
+int lbm_reset(lbm_ctx *ctx);
+
+/* n >= 0 pseudo-time steps of Algorithm 1 (collision + streaming, periodic
+ * wrap by index arithmetic).  Enqueued only. */
+int lbm_iterate(lbm_ctx *ctx, int64_t n);
+
+/* n steps in which every check_every-th step also evaluates the steady-state
+ * residual (fused into that step).  The last residual is written to
+ * out[0..4] if out is non-null: r_inf, r_2, max|u|, ||u||_2, nonfinite flag
+ * (see lbm_solve).  Synchronous when out is non-null. */
+int lbm_iterate_checked(lbm_ctx *ctx, int64_t n, int check_every, double *out);
+
+/* Iterate until the steady-state residual drops below tol (Sec. 2.1:
+ * ||d u/dt|| < TOL "in some norm").  Reading used: every check_every (= k)
+ * steps, r = max_x |u^n - u^(n-k)|_inf / (k max_x |u^n|_inf), accumulated in
+ * FP64 (r = 0 when u = 0).  The first check after a reset only takes the
+ * snapshot.  Stops when r < tol (LBM_OK), when a non-finite displacement
+ * appears (LBM_ERR_DIVERGED) or after max_iters steps
+ * (LBM_ERR_NOT_CONVERGED).  iters_out / residual_out (nullable) receive the
+ * steps taken in this call and the last r.  Synchronous. */
+int lbm_solve(lbm_ctx *ctx, double tol, int64_t max_iters, int check_every,
+              int64_t *iters_out, double *residual_out);
+
+/* Displacement u_x = mbar_10, u_y = mbar_01 (Table 2, Eq. coll10) of the
+ * current state, FP64, into host arrays of nx*ny doubles.  Synchronous. */
+int lbm_get_displacement(lbm_ctx *ctx, double *ux, double *uy);
+
+/* Cauchy stress in lattice units (Table 2 times eps, Eq. compute_bared with
+ * the Table 1 equilibria), FP64, into host arrays of nx*ny.  Synchronous. */
+int lbm_get_stress(lbm_ctx *ctx, double *sxx, double *syy, double *sxy);
+
+/* All five fields (u_x, u_y, sigma_xx, sigma_yy, sigma_xy) into a device
+ * array of 5*nx*ny doubles (plane-major).  Enqueued only. */
+int lbm_get_fields_device(lbm_ctx *ctx, double *out);
+
+/* Pre-collision populations of the current state (8 planes, see above) into
+ * a host array of 8*nx*ny doubles.  Synchronous.  Checkpoint / test hook. */
+int lbm_get_populations(lbm_ctx *ctx, double *f);
+
+/* Overwrite the state with pre-collision populations f (host, 8*nx*ny
+ * doubles, must be finite); rounded to the storage type.  Synchronous. */
+int lbm_set_populations(lbm_ctx *ctx, const double *f);
+
+/* Steps taken since the last reset (or set_populations). */
+int lbm_get_step(lbm_ctx *ctx, int64_t *step);
+
+/* Relaxation rates and theta in use. */
+int lbm_get_rates(lbm_ctx *ctx, lbm_rates *out);
+
+/* Bytes of device memory the context holds. */
+int lbm_get_device_bytes(lbm_ctx *ctx, size_t *bytes);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *lbm_last_error(void);
+
+/* Library version string. */
+const char *lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

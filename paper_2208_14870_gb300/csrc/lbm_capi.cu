@@ -1,0 +1,592 @@
+// lbm_capi.cu -- the C ABI of include/lbm.h: context lifetime, parameter
+// mapping (Table 1), host <-> device transfers and the pseudo-time driver
+// (iterate / solve) around the kernels of lbm_kernels.cuh.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct lbm_ctx {
+    int device = 0;
+    int nx = 0, ny = 0, dtype = 0;
+    int64_t n = 0, plane = 0;
+    lbm_rates rates{};
+    bool gen = false;              // non-standard w_12, w_21, w_22
+    cudaStream_t stream = nullptr;
+    void* pop[2] = {nullptr, nullptr};
+    float* car[2] = {nullptr, nullptr};
+    void* force = nullptr;         // 2 planes of the storage force type
+    double* snap = nullptr;        // 2*n
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+    double* result = nullptr;      // kRes doubles (device)
+    unsigned long long* absmax = nullptr;
+    unsigned int* bad = nullptr;
+    double* pinned = nullptr;      // kRes + 2 doubles (pinned host)
+    double* staging = nullptr;     // FP64 device staging for host transfers
+    int64_t staging_len = 0;
+    int cur = 0;
+    int64_t step = 0;
+    bool snap_valid = false;
+    int64_t snap_step = 0;
+    int hexp = 0;
+    float hscale = 1.0f, hinv = 1.0f;
+    int V = 1;
+    size_t bytes = 0;
+    int64_t nblocks = 0;
+};
+
+namespace {
+
+size_t pop_elem_bytes(int dtype) {
+    return dtype == LBM_F64 ? sizeof(double) : dtype == LBM_F32 ? sizeof(float) : sizeof(__half);
+}
+size_t force_elem_bytes(int dtype) { return dtype == LBM_F64 ? sizeof(double) : sizeof(float); }
+
+StepParams params(const lbm_ctx* c, int src) {
+    StepParams a{};
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.plane = c->plane;
+    a.src = c->pop[src];
+    a.dst = c->pop[src ^ 1];
+    a.csrc = c->car[src];
+    a.cdst = c->car[src ^ 1];
+    a.gx = c->force;
+    a.gy = static_cast<const char*>(c->force) + c->plane * force_elem_bytes(c->dtype);
+    a.hscale = c->hscale;
+    a.hinv = c->hinv;
+    a.snap = c->snap;
+    a.partials = c->partials;
+    a.counter = c->counter;
+    a.result = c->result;
+    return a;
+}
+
+template <typename T>
+Coef<T> coef(const lbm_rates& r) {
+    Coef<T> c;
+    c.a11 = T(1.0 - r.w11);
+    c.as = T(1.0 - r.ws);
+    c.ad = T(1.0 - r.wd);
+    c.w12t = T(r.w12 * r.theta);
+    c.a12 = T(1.0 - r.w12);
+    c.w21t = T(r.w21 * r.theta);
+    c.a21 = T(1.0 - r.w21);
+    c.a22 = T(1.0 - r.w22);
+    c.theta = T(r.theta);
+    c.b11 = T(1.0 - 0.5 * r.w11);
+    c.bs = T(1.0 - 0.5 * r.ws);
+    c.bd = T(1.0 - 0.5 * r.wd);
+    return c;
+}
+
+cudaError_t launch_step(lbm_ctx* c, bool check) {
+    const StepParams a = params(c, c->cur);
+    cudaError_t e;
+    switch (c->dtype) {
+        case LBM_F64: e = Ops<S_F64>::step(a, coef<double>(c->rates), c->V, c->gen, check, c->stream); break;
+        case LBM_F32: e = Ops<S_F32>::step(a, coef<float>(c->rates), c->V, c->gen, check, c->stream); break;
+        default: e = Ops<S_F16S>::step(a, coef<float>(c->rates), c->V, c->gen, check, c->stream); break;
+    }
+    if (e == cudaSuccess) {
+        c->cur ^= 1;
+        c->step += 1;
+    }
+    return e;
+}
+
+cudaError_t launch_fields(lbm_ctx* c, double* out) {
+    const StepParams a = params(c, c->cur);
+    const Coef<double> cd = coef<double>(c->rates);
+    switch (c->dtype) {
+        case LBM_F64: return Ops<S_F64>::fields(a, cd, c->rates.theta, out, c->stream);
+        case LBM_F32: return Ops<S_F32>::fields(a, cd, float(c->rates.theta), out, c->stream);
+        default: return Ops<S_F16S>::fields(a, cd, float(c->rates.theta), out, c->stream);
+    }
+}
+
+int ensure_staging(lbm_ctx* c, int64_t len) {
+    if (c->staging_len >= len) return LBM_OK;
+    if (c->staging) {
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaFree(c->staging));
+        c->bytes -= c->staging_len * sizeof(double);
+        c->staging = nullptr;
+        c->staging_len = 0;
+    }
+    CK(cudaMalloc(&c->staging, len * sizeof(double)));
+    c->staging_len = len;
+    c->bytes += len * sizeof(double);
+    return LBM_OK;
+}
+
+int check_ctx(lbm_ctx* c) {
+    if (!c) return fail(LBM_ERR_ARG, "null context");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != c->device) CK(cudaSetDevice(c->device));
+    return LBM_OK;
+}
+
+void free_all(lbm_ctx* c) {
+    for (int i = 0; i < 2; ++i) {
+        if (c->pop[i]) cudaFree(c->pop[i]);
+        if (c->car[i]) cudaFree(c->car[i]);
+    }
+    if (c->force) cudaFree(c->force);
+    if (c->snap) cudaFree(c->snap);
+    if (c->partials) cudaFree(c->partials);
+    if (c->counter) cudaFree(c->counter);
+    if (c->result) cudaFree(c->result);
+    if (c->absmax) cudaFree(c->absmax);
+    if (c->bad) cudaFree(c->bad);
+    if (c->staging) cudaFree(c->staging);
+    if (c->pinned) cudaFreeHost(c->pinned);
+}
+
+// FP16-shifted storage: pick the power-of-two scale of the stored deviations
+// from the force magnitude.  At steady state the deviations are second
+// moments ~ tau * grad u ~ |g| * L / (2 pi); the scale maps |g| * L to 2^8,
+// leaving 2^7 of headroom below FP16's maximum and keeping values far above
+// its smallest normal.
+int update_half_scale(lbm_ctx* c, const double* gx_dev, const double* gy_dev) {
+    CK(cudaMemsetAsync(c->absmax, 0, sizeof(unsigned long long), c->stream));
+    CK(cudaMemsetAsync(c->bad, 0, sizeof(unsigned int), c->stream));
+    k_absmax<<<1024, 256, 0, c->stream>>>(gx_dev, gy_dev, c->n, c->absmax, c->bad);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->pinned, c->absmax, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->pinned + 1, c->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double gmax;
+    std::memcpy(&gmax, c->pinned, sizeof(double));
+    unsigned int bad;
+    std::memcpy(&bad, c->pinned + 1, sizeof(unsigned int));
+    if (bad) return fail(LBM_ERR_ARG, "lbm_set_force: non-finite force");
+    if (c->dtype != LBM_F16S || gmax == 0.0) return LBM_OK;
+    const double L = double(c->nx > c->ny ? c->nx : c->ny);
+    int e = 8 - (int)std::ceil(std::log2(gmax * L));
+    if (e < -60) e = -60;
+    if (e > 60) e = 60;
+    if (e != c->hexp) {
+        const float factor = std::ldexp(1.0f, e - c->hexp);
+        k_rescale_half<<<1024, 256, 0, c->stream>>>(static_cast<__half*>(c->pop[c->cur]),
+                                                   8 * c->plane, factor);
+        CK(cudaGetLastError());
+        c->hexp = e;
+        c->hscale = std::ldexp(1.0f, e);
+        c->hinv = std::ldexp(1.0f, -e);
+    }
+    return LBM_OK;
+}
+
+int set_force_dev(lbm_ctx* c, const double* gx, const double* gy) {
+    if (c->dtype == LBM_F64) {
+        CK(cudaMemcpyAsync(c->force, gx, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(static_cast<double*>(c->force) + c->plane, gy, c->n * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        float* fx = static_cast<float*>(c->force);
+        k_force_convert<float><<<2048, 256, 0, c->stream>>>(gx, gy, fx, fx + c->plane, c->n);
+        CK(cudaGetLastError());
+    }
+    if (c->dtype == LBM_F16S) return update_half_scale(c, gx, gy);
+    return LBM_OK;
+}
+
+// Reads the residual of the last check; returns r_inf etc. in out[0..4].
+int read_residual(lbm_ctx* c, double out[kRes]) {
+    CK(cudaMemcpyAsync(c->pinned, c->result, kRes * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < kRes; ++k) out[k] = c->pinned[k];
+    return LBM_OK;
+}
+
+// Convert the raw reduction [max|du|, max|u|, sum du^2, sum u^2, bad] over a
+// window of `steps` steps into [r_inf, r_2, max|u|, ||u||_2, bad].
+void finish_residual(const double raw[kRes], int64_t steps, double out[kRes]) {
+    const double k = double(steps > 0 ? steps : 1);
+    out[0] = raw[1] > 0.0 ? raw[0] / (k * raw[1]) : 0.0;
+    out[1] = raw[3] > 0.0 ? std::sqrt(raw[2]) / (k * std::sqrt(raw[3])) : 0.0;
+    out[2] = raw[1];
+    out[3] = std::sqrt(raw[3]);
+    out[4] = raw[4];
+    if (raw[4] != 0.0 || !std::isfinite(raw[0]) || !std::isfinite(raw[1])) {
+        out[0] = out[1] = INFINITY;
+        out[4] = 1.0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+const char* lbm_version(void) { return "gb300-lbm-elastic 0.1 (sm_103a)"; }
+
+int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm_options* opt,
+                  lbm_ctx** out) {
+    if (!out) return fail(LBM_ERR_ARG, "lbm_create: null output pointer");
+    *out = nullptr;
+    if (nx < 1 || ny < 1) return fail(LBM_ERR_ARG, "lbm_create: nx and ny must be >= 1");
+    if ((int64_t)nx * ny > (int64_t)1 << 34)
+        return fail(LBM_ERR_ARG, "lbm_create: lattice larger than 2^34 nodes");
+    if (!std::isfinite(lambda) || !std::isfinite(mu))
+        return fail(LBM_ERR_ARG, "lbm_create: non-finite Lame parameter");
+    if (!(mu > 0.0)) return fail(LBM_ERR_ARG, "lbm_create: mu must be > 0");
+    if (!(lambda + mu > 0.0)) return fail(LBM_ERR_ARG, "lbm_create: lambda + mu must be > 0");
+    if (dtype != LBM_F64 && dtype != LBM_F32 && dtype != LBM_F16S)
+        return fail(LBM_ERR_ARG, "lbm_create: unknown dtype");
+    double theta = 1.0 / 3.0, tau12 = 0.5, tau22 = 0.5;
+    if (opt) {
+        if (opt->theta != 0.0) theta = opt->theta;
+        if (opt->tau12 != 0.0) tau12 = opt->tau12;
+        if (opt->tau22 != 0.0) tau22 = opt->tau22;
+    }
+    if (!(theta > 0.0 && theta < 1.0)) return fail(LBM_ERR_ARG, "lbm_create: theta must be in (0, 1)");
+    if (!(tau12 > -0.5) || !(tau22 > -0.5) || !std::isfinite(tau12) || !std::isfinite(tau22))
+        return fail(LBM_ERR_ARG, "lbm_create: tau12, tau22 must be finite and > -1/2");
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(LBM_ERR_OOM, "lbm_create: host allocation failed");
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    c->nx = nx;
+    c->ny = ny;
+    c->dtype = dtype;
+    c->n = (int64_t)nx * ny;
+    c->plane = round_up(c->n, 128);
+    // Table 1 and Eq. relaxation_rate: theta tau_11 = mu, (1-theta)/2 tau_d = mu,
+    // (1+theta)/2 tau_s = K = lambda + mu, w = 1/(tau + 1/2).
+    const double K = lambda + mu;
+    const double tau11 = mu / theta, taud = 2.0 * mu / (1.0 - theta), taus = 2.0 * K / (1.0 + theta);
+    c->rates.w11 = 1.0 / (tau11 + 0.5);
+    c->rates.ws = 1.0 / (taus + 0.5);
+    c->rates.wd = 1.0 / (taud + 0.5);
+    c->rates.w12 = 1.0 / (tau12 + 0.5);
+    c->rates.w21 = c->rates.w12;
+    c->rates.w22 = 1.0 / (tau22 + 0.5);
+    c->rates.theta = theta;
+    c->gen = !(c->rates.w12 == 1.0 && c->rates.w22 == 1.0);
+    if (dtype == LBM_F64) c->V = nx >= 64 ? 2 : 1;
+    else c->V = nx >= 128 ? 4 : 1;
+    const dim3 g = step_grid(nx, ny, c->V);
+    c->nblocks = (int64_t)g.x * g.y;
+
+    const size_t pb = pop_elem_bytes(dtype) * 8 * c->plane;
+    const size_t fb = force_elem_bytes(dtype) * 2 * c->plane;
+    const size_t cb = sizeof(float) * 2 * c->plane;
+    auto alloc = [&](void** p, size_t bytes) -> cudaError_t {
+        cudaError_t r = cudaMalloc(p, bytes);
+        if (r == cudaSuccess) c->bytes += bytes;
+        return r;
+    };
+    e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = alloc(&c->pop[i], pb);
+        if (e == cudaSuccess && dtype == LBM_F16S) e = alloc((void**)&c->car[i], cb);
+    }
+    if (e == cudaSuccess) e = alloc(&c->force, fb);
+    if (e == cudaSuccess) e = alloc((void**)&c->snap, sizeof(double) * 2 * c->n);
+    if (e == cudaSuccess) e = alloc((void**)&c->partials, sizeof(double) * kRes * c->nblocks);
+    if (e == cudaSuccess) e = alloc((void**)&c->counter, sizeof(unsigned int));
+    if (e == cudaSuccess) e = alloc((void**)&c->result, sizeof(double) * kRes);
+    if (e == cudaSuccess) e = alloc((void**)&c->absmax, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = alloc((void**)&c->bad, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, sizeof(double) * (kRes + 2));
+    if (e == cudaSuccess) e = cudaMemset(c->pop[0], 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(c->pop[1], 0, pb);
+    if (e == cudaSuccess && dtype == LBM_F16S) e = cudaMemset(c->car[0], 0, cb);
+    if (e == cudaSuccess && dtype == LBM_F16S) e = cudaMemset(c->car[1], 0, cb);
+    if (e == cudaSuccess) e = cudaMemset(c->force, 0, fb);
+    if (e == cudaSuccess) e = cudaMemset(c->snap, 0, sizeof(double) * 2 * c->n);
+    if (e == cudaSuccess) e = cudaMemset(c->counter, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        int code = cuda_fail(e, "lbm_create: device allocation");
+        free_all(c);
+        delete c;
+        return code;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_create(int nx, int ny, double lambda, double mu, int dtype, lbm_ctx** out) {
+    return lbm_create_ex(nx, ny, lambda, mu, dtype, nullptr, out);
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev != c->device) cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    if (dev >= 0 && dev != c->device) cudaSetDevice(dev);
+    delete c;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+int lbm_set_force(lbm_ctx* c, const double* gx, const double* gy) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!gx || !gy) return fail(LBM_ERR_ARG, "lbm_set_force: null pointer");
+    rc = ensure_staging(c, 2 * c->n);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->staging, gx, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->staging + c->n, gy, c->n * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    rc = set_force_dev(c, c->staging, c->staging + c->n);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_force_device(lbm_ctx* c, const double* gx, const double* gy) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!gx || !gy) return fail(LBM_ERR_ARG, "lbm_set_force_device: null pointer");
+    return set_force_dev(c, gx, gy);
+}
+
+int lbm_reset(lbm_ctx* c) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(c->pop[c->cur], 0, pop_elem_bytes(c->dtype) * 8 * c->plane, c->stream));
+    if (c->dtype == LBM_F16S)
+        CK(cudaMemsetAsync(c->car[c->cur], 0, sizeof(float) * 2 * c->plane, c->stream));
+    c->step = 0;
+    c->snap_valid = false;
+    return LBM_OK;
+}
+
+int lbm_iterate(lbm_ctx* c, int64_t n) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n < 0) return fail(LBM_ERR_ARG, "lbm_iterate: n must be >= 0");
+    for (int64_t i = 0; i < n; ++i) {
+        cudaError_t e = launch_step(c, false);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_iterate: step launch");
+    }
+    return LBM_OK;
+}
+
+int lbm_iterate_checked(lbm_ctx* c, int64_t n, int check_every, double* out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n < 0 || check_every < 1) return fail(LBM_ERR_ARG, "lbm_iterate_checked: bad n or check_every");
+    int64_t last_window = 0;
+    bool any = false;
+    for (int64_t i = 0; i < n; ++i) {
+        const bool check = ((c->step + 1) % check_every) == 0;
+        cudaError_t e = launch_step(c, check);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_iterate_checked: step launch");
+        if (check) {
+            last_window = c->snap_valid ? c->step - c->snap_step : 0;
+            any = c->snap_valid;
+            c->snap_valid = true;
+            c->snap_step = c->step;
+        }
+    }
+    if (out) {
+        double raw[kRes];
+        rc = read_residual(c, raw);
+        if (rc) return rc;
+        if (any) finish_residual(raw, last_window, out);
+        else {
+            finish_residual(raw, 1, out);
+            out[0] = out[1] = INFINITY;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_solve(lbm_ctx* c, double tol, int64_t max_iters, int check_every, int64_t* iters_out,
+              double* residual_out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!(tol >= 0.0) || max_iters < 0 || check_every < 1)
+        return fail(LBM_ERR_ARG, "lbm_solve: bad tol, max_iters or check_every");
+    int64_t done = 0;
+    double r = INFINITY;
+    int status = LBM_ERR_NOT_CONVERGED;
+    while (done < max_iters) {
+        const int64_t to_check = check_every - (c->step % check_every);
+        const int64_t plain = to_check - 1;
+        if (done + to_check > max_iters) {
+            rc = lbm_iterate(c, max_iters - done);
+            if (rc) return rc;
+            done = max_iters;
+            break;
+        }
+        rc = lbm_iterate(c, plain);
+        if (rc) return rc;
+        cudaError_t e = launch_step(c, true);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_solve: check launch");
+        done += to_check;
+        double raw[kRes], res[kRes];
+        rc = read_residual(c, raw);
+        if (rc) return rc;
+        const bool had = c->snap_valid;
+        const int64_t window = c->step - c->snap_step;
+        c->snap_valid = true;
+        c->snap_step = c->step;
+        finish_residual(raw, window, res);
+        if (res[4] != 0.0) {
+            status = LBM_ERR_DIVERGED;
+            r = INFINITY;
+            break;
+        }
+        if (!had) continue;
+        r = res[0];
+        if (r < tol) {
+            status = LBM_OK;
+            break;
+        }
+    }
+    if (iters_out) *iters_out = done;
+    if (residual_out) *residual_out = r;
+    if (status == LBM_ERR_DIVERGED) return fail(status, "lbm_solve: non-finite displacement (diverged)");
+    if (status == LBM_ERR_NOT_CONVERGED) return fail(status, "lbm_solve: max_iters reached above tolerance");
+    return LBM_OK;
+}
+
+int lbm_get_fields_device(lbm_ctx* c, double* out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!out) return fail(LBM_ERR_ARG, "lbm_get_fields_device: null pointer");
+    CK(launch_fields(c, out));
+    return LBM_OK;
+}
+
+int lbm_get_displacement(lbm_ctx* c, double* ux, double* uy) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!ux || !uy) return fail(LBM_ERR_ARG, "lbm_get_displacement: null pointer");
+    rc = ensure_staging(c, 5 * c->n);
+    if (rc) return rc;
+    CK(launch_fields(c, c->staging));
+    CK(cudaMemcpyAsync(ux, c->staging, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(uy, c->staging + c->n, c->n * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_get_stress(lbm_ctx* c, double* sxx, double* syy, double* sxy) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!sxx || !syy || !sxy) return fail(LBM_ERR_ARG, "lbm_get_stress: null pointer");
+    rc = ensure_staging(c, 5 * c->n);
+    if (rc) return rc;
+    CK(launch_fields(c, c->staging));
+    double* outs[3] = {sxx, syy, sxy};
+    for (int k = 0; k < 3; ++k)
+        CK(cudaMemcpyAsync(outs[k], c->staging + (2 + k) * c->n, c->n * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!f) return fail(LBM_ERR_ARG, "lbm_get_populations: null pointer");
+    rc = ensure_staging(c, 8 * c->n);
+    if (rc) return rc;
+    const StepParams a = params(c, c->cur);
+    cudaError_t e;
+    switch (c->dtype) {
+        case LBM_F64: e = Ops<S_F64>::export_pop(a, c->rates.theta, c->staging, c->stream); break;
+        case LBM_F32: e = Ops<S_F32>::export_pop(a, float(c->rates.theta), c->staging, c->stream); break;
+        default: e = Ops<S_F16S>::export_pop(a, float(c->rates.theta), c->staging, c->stream); break;
+    }
+    CK(e);
+    CK(cudaMemcpyAsync(f, c->staging, 8 * c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!f) return fail(LBM_ERR_ARG, "lbm_set_populations: null pointer");
+    for (int64_t i = 0; i < 8 * c->n; ++i)
+        if (!std::isfinite(f[i])) return fail(LBM_ERR_ARG, "lbm_set_populations: non-finite value");
+    rc = ensure_staging(c, 8 * c->n);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->staging, f, 8 * c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const StepParams a = params(c, c->cur ^ 1);  // dst = current buffer
+    cudaError_t e;
+    switch (c->dtype) {
+        case LBM_F64: e = Ops<S_F64>::import_pop(a, c->rates.theta, c->staging, c->stream); break;
+        case LBM_F32: e = Ops<S_F32>::import_pop(a, float(c->rates.theta), c->staging, c->stream); break;
+        default: e = Ops<S_F16S>::import_pop(a, float(c->rates.theta), c->staging, c->stream); break;
+    }
+    CK(e);
+    CK(cudaStreamSynchronize(c->stream));
+    c->step = 0;
+    c->snap_valid = false;
+    return LBM_OK;
+}
+
+int lbm_get_step(lbm_ctx* c, int64_t* step) {
+    if (!c || !step) return fail(LBM_ERR_ARG, "lbm_get_step: null pointer");
+    *step = c->step;
+    return LBM_OK;
+}
+
+int lbm_get_rates(lbm_ctx* c, lbm_rates* out) {
+    if (!c || !out) return fail(LBM_ERR_ARG, "lbm_get_rates: null pointer");
+    *out = c->rates;
+    return LBM_OK;
+}
+
+int lbm_get_device_bytes(lbm_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(LBM_ERR_ARG, "lbm_get_device_bytes: null pointer");
+    *bytes = c->bytes;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// lbm_core.cuh -- per-node arithmetic of the periodic lattice Boltzmann scheme
+// for linear elasticity (Boolakee, Geier, De Lorenzis, arXiv 2208.14870),
+// shared by every kernel of the library.
+//
+// Populations are kept in the paper's one-index order (Sec. 4, population
+// table): c_1..c_8 = (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1),
+// stored here as f[0..7].  Moments use the paper's moment order
+// 10, 01, 11, s, d, 12, 21, 22 (Sec. 4, moment table).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Moments of the collision basis.
+template <typename T>
+struct Mom {
+    T m10, m01, m11, ms, md, m12, m21, m22;
+};
+
+// Per-lattice constants of the collision in compute precision.
+//   a11 = 1 - w11, as = 1 - ws, ad = 1 - wd          (Eq. collision, m^eq = 0)
+//   w12t = w12 * theta, a12 = 1 - w12, ...            (m^eq_12 = theta mbar_10)
+template <typename T>
+struct Coef {
+    T a11, as, ad;
+    T w12t, a12, w21t, a21, a22;
+    T theta;
+    T b11, bs, bd;   // 1 - w/2 (bared moments, Eq. compute_bared)
+};
+
+// Raw moments of eight populations, Eq. moments and Eq. replace_raw, written
+// as a butterfly: with p = f5 + f7, q = f6 + f8, r = f5 - f7, s = f6 - f8,
+//   m11 = p - q, m22 = p + q, m12 = r - s, m21 = r + s,
+//   m10 = (f1 - f3) + m12, m01 = (f2 - f4) + m21,
+//   ms = (f1 + f3) + (f2 + f4) + 2 m22, md = (f1 + f3) - (f2 + f4).
+template <typename T>
+__device__ __forceinline__ Mom<T> moments(const T f[8]) {
+    Mom<T> m;
+    const T p = f[4] + f[6], q = f[5] + f[7];
+    const T r = f[4] - f[6], s = f[5] - f[7];
+    m.m11 = p - q;
+    m.m22 = p + q;
+    m.m12 = r - s;
+    m.m21 = r + s;
+    m.m10 = (f[0] - f[2]) + m.m12;
+    m.m01 = (f[1] - f[3]) + m.m21;
+    const T s13 = f[0] + f[2], s24 = f[1] + f[3];
+    m.ms = (s13 + s24) + T(2) * m.m22;
+    m.md = s13 - s24;
+    return m;
+}
+
+// Collision in moment space (Algorithm 1, collision block):
+//   mbar_10 = m_10 + g_x/2, mbar_01 = m_01 + g_y/2          (Eqs. coll10, coll01)
+//   m*_a = w_a m^eq_a + (1 - w_a) m_a, Table 1 equilibria  (Eq. collision)
+//   m*_10 = mbar_10 + g_x/2, m*_01 = mbar_01 + g_y/2       (Eqs. coll10post, coll01post)
+// GEN = false is the standard case w_12 = w_21 = w_22 = 1 (Sec. 3.3.2),
+// where m*_12 = theta u, m*_21 = theta v, m*_22 = 0.
+// u, v receive the displacement mbar_10, mbar_01 (Table 2).
+template <typename T, bool GEN>
+__device__ __forceinline__ Mom<T> collide(const Mom<T>& m, T gx, T gy, const Coef<T>& c,
+                                          T& u, T& v) {
+    Mom<T> s;
+    u = m.m10 + T(0.5) * gx;
+    v = m.m01 + T(0.5) * gy;
+    s.m10 = m.m10 + gx;
+    s.m01 = m.m01 + gy;
+    s.m11 = c.a11 * m.m11;
+    s.ms = c.as * m.ms;
+    s.md = c.ad * m.md;
+    if (GEN) {
+        s.m12 = c.w12t * u + c.a12 * m.m12;
+        s.m21 = c.w21t * v + c.a21 * m.m21;
+        s.m22 = c.a22 * m.m22;
+    } else {
+        s.m12 = c.theta * u;
+        s.m21 = c.theta * v;
+        s.m22 = T(0);
+    }
+    return s;
+}
+
+// Back-transformation f = M^-1 m (Eq. moments_post solved in closed form):
+//   A = m10 - m12, B = m01 - m21, P = (ms - 2 m22 + md)/2, Q = (ms - 2 m22 - md)/2
+//   f1 = (P + A)/2, f3 = (P - A)/2, f2 = (Q + B)/2, f4 = (Q - B)/2
+//   f5 = (m22 + m11 + m12 + m21)/4, f6 = (m22 - m11 - m12 + m21)/4,
+//   f7 = (m22 + m11 - m12 - m21)/4, f8 = (m22 - m11 + m12 - m21)/4.
+template <typename T>
+__device__ __forceinline__ void populations(const Mom<T>& s, T f[8]) {
+    const T A = s.m10 - s.m12, B = s.m01 - s.m21;
+    const T t = s.ms - T(2) * s.m22;
+    const T P = T(0.25) * (t + s.md), Q = T(0.25) * (t - s.md);
+    f[0] = P + T(0.5) * A;
+    f[2] = P - T(0.5) * A;
+    f[1] = Q + T(0.5) * B;
+    f[3] = Q - T(0.5) * B;
+    const T h1 = s.m22 + s.m11, h2 = s.m22 - s.m11;
+    const T h3 = s.m12 + s.m21, h4 = s.m21 - s.m12;
+    f[4] = T(0.25) * (h1 + h3);
+    f[6] = T(0.25) * (h1 - h3);
+    f[5] = T(0.25) * (h2 + h4);
+    f[7] = T(0.25) * (h2 - h4);
+}
+
+// Shifted FP16 storage.  The equilibrium-type part of a post-collision state
+// with first moments (c10, c01) is E = M^-1 (c10, c01, 0, 0, 0, theta c10,
+// theta c01, 0):
+//   E1 = k1 c10, E3 = -k1 c10, E2 = k1 c01, E4 = -k1 c01   (k1 = (1 - theta)/2)
+//   E5 = k5 (c10 + c01), E6 = k5 (c01 - c10), E7 = -k5 (c10 + c01),
+//   E8 = k5 (c10 - c01)                                     (k5 = theta/4)
+// The stored deviation is N = f* - E = M^-1 (0, 0, m*_11, m*_s, m*_d,
+// m*_12 - theta m*_10, m*_21 - theta m*_01, m*_22), which is O(eps) of f*.
+template <typename T>
+__device__ __forceinline__ Mom<T> deviation_moments(const Mom<T>& s, T theta) {
+    Mom<T> n = s;
+    n.m10 = T(0);
+    n.m01 = T(0);
+    n.m12 = s.m12 - theta * s.m10;
+    n.m21 = s.m21 - theta * s.m01;
+    return n;
+}
+
+__device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int wrap_inc(int i, int n) { return i + 1 == n ? 0 : i + 1; }
+
+}  // namespace lbm

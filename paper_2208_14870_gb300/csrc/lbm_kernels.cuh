@@ -1,0 +1,380 @@
+// lbm_kernels.cuh -- CUDA kernels of the periodic lattice Boltzmann scheme for
+// linear elasticity (arXiv 2208.14870): fused stream-collide step (Algorithm 1)
+// with an optional fused steady-state residual, solution recovery (Table 2),
+// population import/export and force upload.  Instantiated once per storage
+// type by lbm_step_f64.cu, lbm_step_f32.cu and lbm_step_f16s.cu.
+//
+// Memory layout (structure of arrays): population p of node (x, y) lives at
+// base + p*plane + y*nx + x; `plane` >= nx*ny is padded to 256 bytes.  The
+// stored state between steps is the post-collision population f*_p(x) of the
+// previous step ("pull" scheme): a step gathers f_p(x) = f*_p(x - c_p) with the
+// periodic wrap done by index arithmetic (Sec. 5.1), collides, and writes
+// f*_p(x) to the other buffer of a ping-pong pair.
+//
+// Thread mapping: a block of 32 x BY threads covers a tile of 32*V columns by
+// BY rows; a thread handles V nodes of one row spaced 32 apart, so each warp
+// load or store instruction touches 32 consecutive nodes of one plane.
+#pragma once
+
+#include "lbm_core.cuh"
+
+namespace lbm {
+
+constexpr int BY = 8;              // rows per block (block = 32 x BY threads)
+constexpr int kThreads = 32 * BY;
+
+enum Storage { S_F64 = 0, S_F32 = 1, S_F16S = 2 };
+
+template <int S> struct StoreT;
+template <> struct StoreT<S_F64> { using T = double; using P = double; using G = double; };
+template <> struct StoreT<S_F32> { using T = float; using P = float; using G = float; };
+template <> struct StoreT<S_F16S> { using T = float; using P = __half; using G = float; };
+
+// Residual partial sums of one block: max|du|, max|u|, sum du^2, sum u^2,
+// non-finite flag.
+constexpr int kRes = 5;
+
+struct StepParams {
+    int nx, ny;
+    int64_t plane;          // elements between planes
+    const void* src;        // 8 population planes (storage type)
+    void* dst;
+    const float* csrc;      // F16S: carrier planes m*_10, m*_01 (FP32, stride plane)
+    float* cdst;
+    const void* gx;         // force planes (G)
+    const void* gy;
+    float hscale;           // F16S: stored = deviation * hscale (power of two)
+    float hinv;             // 1 / hscale
+    double* snap;           // residual: u_x, u_y snapshot, 2 planes of nx*ny FP64
+    double* partials;       // residual: kRes doubles per block
+    unsigned int* counter;  // residual: blocks finished (reset by the last block)
+    double* result;         // residual: kRes doubles
+};
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_h(const __half* p) { return __half2float(__ldg(p)); }
+
+// Gather the pre-collision populations of node (x, y): f_p(x) = f*_p(x - c_p).
+// r0, rm, rp: offsets of rows y, y-1, y+1 (wrapped); xm, xp: columns x-1, x+1.
+template <int S>
+__device__ __forceinline__ void gather(const StepParams& a, int64_t r0, int64_t rm, int64_t rp,
+                                       int x, int xm, int xp, typename StoreT<S>::T f[8],
+                                       typename StoreT<S>::T theta) {
+    using T = typename StoreT<S>::T;
+    using P = typename StoreT<S>::P;
+    const P* s = static_cast<const P*>(a.src);
+    const int64_t pl = a.plane;
+    const int64_t i0 = r0 + xm, i1 = rm + x, i2 = r0 + xp, i3 = rp + x;
+    const int64_t i4 = rm + xm, i5 = rm + xp, i6 = rp + xp, i7 = rp + xm;
+    if constexpr (S == S_F16S) {
+        const float hinv = a.hinv;
+        const float* c10 = a.csrc;
+        const float* c01 = a.csrc + pl;
+        const float k1 = 0.5f * (1.0f - theta), k5 = 0.25f * theta;
+        f[0] = ld_h(s + 0 * pl + i0) * hinv + k1 * ldg(c10 + i0);
+        f[1] = ld_h(s + 1 * pl + i1) * hinv + k1 * ldg(c01 + i1);
+        f[2] = ld_h(s + 2 * pl + i2) * hinv - k1 * ldg(c10 + i2);
+        f[3] = ld_h(s + 3 * pl + i3) * hinv - k1 * ldg(c01 + i3);
+        f[4] = ld_h(s + 4 * pl + i4) * hinv + k5 * (ldg(c10 + i4) + ldg(c01 + i4));
+        f[5] = ld_h(s + 5 * pl + i5) * hinv + k5 * (ldg(c01 + i5) - ldg(c10 + i5));
+        f[6] = ld_h(s + 6 * pl + i6) * hinv - k5 * (ldg(c10 + i6) + ldg(c01 + i6));
+        f[7] = ld_h(s + 7 * pl + i7) * hinv + k5 * (ldg(c10 + i7) - ldg(c01 + i7));
+    } else {
+        (void)theta;
+        f[0] = T(ldg(s + 0 * pl + i0));
+        f[1] = T(ldg(s + 1 * pl + i1));
+        f[2] = T(ldg(s + 2 * pl + i2));
+        f[3] = T(ldg(s + 3 * pl + i3));
+        f[4] = T(ldg(s + 4 * pl + i4));
+        f[5] = T(ldg(s + 5 * pl + i5));
+        f[6] = T(ldg(s + 6 * pl + i6));
+        f[7] = T(ldg(s + 7 * pl + i7));
+    }
+}
+
+// Store the post-collision state of node idx.
+template <int S>
+__device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
+                                              const Mom<typename StoreT<S>::T>& s,
+                                              typename StoreT<S>::T theta) {
+    using T = typename StoreT<S>::T;
+    using P = typename StoreT<S>::P;
+    P* d = static_cast<P*>(a.dst);
+    const int64_t pl = a.plane;
+    T f[8];
+    if constexpr (S == S_F16S) {
+        populations(deviation_moments(s, theta), f);
+        const float hs = a.hscale;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) d[p * pl + idx] = __float2half_rn(f[p] * hs);
+        a.cdst[idx] = s.m10;
+        a.cdst[pl + idx] = s.m01;
+    } else {
+        (void)theta;
+        populations(s, f);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) d[p * pl + idx] = P(f[p]);
+    }
+}
+
+// Block-wide reduction of the residual partials followed by the grid-level
+// pass: the last block to finish (counted with an atomic) reduces all block
+// partials and writes the result, then resets the counter for the next check.
+__device__ __forceinline__ void residual_reduce(const StepParams& a, double v[kRes]) {
+    __shared__ double sh[kRes][kThreads / 32];
+    __shared__ bool is_last;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
+        v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
+        v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], o));
+    }
+    if (lane == 0)
+        for (int k = 0; k < kRes; ++k) sh[k][warp] = v[k];
+    __syncthreads();
+    const unsigned int nblocks = gridDim.x * gridDim.y;
+    const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (warp == 0) {
+        double w[kRes];
+        for (int k = 0; k < kRes; ++k) w[k] = (lane < nwarps) ? sh[k][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w[0] = fmax(w[0], __shfl_xor_sync(0xffffffffu, w[0], o));
+            w[1] = fmax(w[1], __shfl_xor_sync(0xffffffffu, w[1], o));
+            w[2] += __shfl_xor_sync(0xffffffffu, w[2], o);
+            w[3] += __shfl_xor_sync(0xffffffffu, w[3], o);
+            w[4] = fmax(w[4], __shfl_xor_sync(0xffffffffu, w[4], o));
+        }
+        if (lane == 0) {
+            for (int k = 0; k < kRes; ++k) a.partials[(int64_t)bid * kRes + k] = w[k];
+            __threadfence();
+            const unsigned int done = atomicAdd(a.counter, 1u);
+            is_last = (done == nblocks - 1);
+        }
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double w[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (unsigned int b = tid; b < nblocks; b += blockDim.x * blockDim.y) {
+        const double* p = a.partials + (int64_t)b * kRes;
+        w[0] = fmax(w[0], __ldcg(p + 0));
+        w[1] = fmax(w[1], __ldcg(p + 1));
+        w[2] += __ldcg(p + 2);
+        w[3] += __ldcg(p + 3);
+        w[4] = fmax(w[4], __ldcg(p + 4));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        w[0] = fmax(w[0], __shfl_xor_sync(0xffffffffu, w[0], o));
+        w[1] = fmax(w[1], __shfl_xor_sync(0xffffffffu, w[1], o));
+        w[2] += __shfl_xor_sync(0xffffffffu, w[2], o);
+        w[3] += __shfl_xor_sync(0xffffffffu, w[3], o);
+        w[4] = fmax(w[4], __shfl_xor_sync(0xffffffffu, w[4], o));
+    }
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < kRes; ++k) sh[k][warp] = w[k];
+    __syncthreads();
+    if (tid == 0) {
+        double r[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < nwarps; ++i) {
+            r[0] = fmax(r[0], sh[0][i]);
+            r[1] = fmax(r[1], sh[1][i]);
+            r[2] += sh[2][i];
+            r[3] += sh[3][i];
+            r[4] = fmax(r[4], sh[4][i]);
+        }
+        for (int k = 0; k < kRes; ++k) a.result[k] = r[k];
+        *a.counter = 0u;
+        __threadfence();
+    }
+}
+
+// One pseudo-time step (Algorithm 1) over the whole lattice.  CHECK adds the
+// steady-state residual: u^n is compared with the snapshot u^(n-k), the
+// snapshot is overwritten with u^n, and max/L2 partials are reduced in FP64.
+template <int S, int V, bool GEN, bool CHECK>
+__global__ void __launch_bounds__(kThreads)
+k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
+    using T = typename StoreT<S>::T;
+    using G = typename StoreT<S>::G;
+    const int nx = a.nx, ny = a.ny;
+    const int y = blockIdx.y * BY + threadIdx.y;
+    const int xb = blockIdx.x * (32 * V) + threadIdx.x;
+    double acc[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (y < ny) {
+        const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
+        const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+        const G* __restrict__ gxp = static_cast<const G*>(a.gx);
+        const G* __restrict__ gyp = static_cast<const G*>(a.gy);
+        // Phase 1: issue every load of the thread's V nodes before any store,
+        // so that up to V*10 loads are in flight per thread.
+        T f[V][8], gx[V], gy[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int x = xb + 32 * j;
+            if (x < nx) {
+                gather<S>(a, r0, rm, rp, x, wrap_dec(x, nx), wrap_inc(x, nx), f[j], c.theta);
+                gx[j] = T(ldg(gxp + r0 + x));
+                gy[j] = T(ldg(gyp + r0 + x));
+            }
+        }
+        // Phase 2: collide and store.
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int x = xb + 32 * j;
+            if (x < nx) {
+                const int64_t idx = r0 + x;
+                T u, v;
+                const Mom<T> s = collide<T, GEN>(moments(f[j]), gx[j], gy[j], c, u, v);
+                scatter_local<S>(a, idx, s, c.theta);
+                if (CHECK) {
+                    const double ud = double(u), vd = double(v);
+                    const int64_t n = (int64_t)nx * ny;
+                    const double uo = a.snap[idx], vo = a.snap[n + idx];
+                    a.snap[idx] = ud;
+                    a.snap[n + idx] = vd;
+                    const double du = ud - uo, dv = vd - vo;
+                    acc[0] = fmax(acc[0], fmax(fabs(du), fabs(dv)));
+                    acc[1] = fmax(acc[1], fmax(fabs(ud), fabs(vd)));
+                    acc[2] += du * du + dv * dv;
+                    acc[3] += ud * ud + vd * vd;
+                    if (!(isfinite(ud) && isfinite(vd))) acc[4] = 1.0;
+                }
+            }
+        }
+    }
+    if (CHECK) residual_reduce(a, acc);
+}
+
+// Solution fields of the current state (Table 2, Eq. compute_bared), FP64:
+// out planes u_x, u_y, sigma_xx, sigma_yy, sigma_xy (stride nx*ny).
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_fields(const StepParams a, const Coef<double> c, typename StoreT<S>::T theta, double* out) {
+    using T = typename StoreT<S>::T;
+    using G = typename StoreT<S>::G;
+    const int nx = a.nx, ny = a.ny;
+    const int y = blockIdx.y * BY + threadIdx.y;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    if (y >= ny || x >= nx) return;
+    const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
+    const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+    T f[8];
+    gather<S>(a, r0, rm, rp, x, wrap_dec(x, nx), wrap_inc(x, nx), f, theta);
+    double fd[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) fd[p] = double(f[p]);
+    const Mom<double> m = moments(fd);
+    const int64_t idx = r0 + x, n = (int64_t)nx * ny;
+    const double gx = double(static_cast<const G*>(a.gx)[idx]);
+    const double gy = double(static_cast<const G*>(a.gy)[idx]);
+    const double mb11 = c.b11 * m.m11, mbs = c.bs * m.ms, mbd = c.bd * m.md;
+    out[idx] = m.m10 + 0.5 * gx;
+    out[n + idx] = m.m01 + 0.5 * gy;
+    out[2 * n + idx] = -0.5 * (mbs + mbd);
+    out[3 * n + idx] = -0.5 * (mbs - mbd);
+    out[4 * n + idx] = -mb11;
+}
+
+// Pre-collision populations of the current state into 8 FP64 planes.
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_export(const StepParams a, typename StoreT<S>::T theta, double* out) {
+    using T = typename StoreT<S>::T;
+    const int nx = a.nx, ny = a.ny;
+    const int y = blockIdx.y * BY + threadIdx.y;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    if (y >= ny || x >= nx) return;
+    const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
+    const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+    T f[8];
+    gather<S>(a, r0, rm, rp, x, wrap_dec(x, nx), wrap_inc(x, nx), f, theta);
+    const int64_t idx = r0 + x, n = (int64_t)nx * ny;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) out[p * n + idx] = double(f[p]);
+}
+
+// Load pre-collision populations f (8 FP64 planes): the stored post-collision
+// value at x is f*_p(x) = f_p(x + c_p) (inverse of the pull gather).
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+k_import(const StepParams a, typename StoreT<S>::T theta, const double* in) {
+    using T = typename StoreT<S>::T;
+    using P = typename StoreT<S>::P;
+    const int nx = a.nx, ny = a.ny;
+    const int y = blockIdx.y * BY + threadIdx.y;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    if (y >= ny || x >= nx) return;
+    const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
+    const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
+    const int64_t n = (int64_t)nx * ny;
+    const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+    // f*_p(x) = f_p(x + c_p)
+    T fs[8];
+    fs[0] = T(in[0 * n + r0 + xp]);
+    fs[1] = T(in[1 * n + rp + x]);
+    fs[2] = T(in[2 * n + r0 + xm]);
+    fs[3] = T(in[3 * n + rm + x]);
+    fs[4] = T(in[4 * n + rp + xp]);
+    fs[5] = T(in[5 * n + rp + xm]);
+    fs[6] = T(in[6 * n + rm + xm]);
+    fs[7] = T(in[7 * n + rm + xp]);
+    const int64_t idx = r0 + x;
+    P* d = static_cast<P*>(a.dst);
+    if constexpr (S == S_F16S) {
+        const Mom<T> s = moments(fs);
+        T nf[8];
+        populations(deviation_moments(s, theta), nf);
+        for (int p = 0; p < 8; ++p) d[p * a.plane + idx] = __float2half_rn(nf[p] * a.hscale);
+        a.cdst[idx] = s.m10;
+        a.cdst[a.plane + idx] = s.m01;
+    } else {
+        (void)theta;
+        for (int p = 0; p < 8; ++p) d[p * a.plane + idx] = P(fs[p]);
+    }
+}
+
+// Force upload: FP64 device arrays -> storage force type.
+template <typename G>
+__global__ void k_force_convert(const double* gx, const double* gy, G* ox, G* oy, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ox[i] = G(gx[i]);
+        oy[i] = G(gy[i]);
+    }
+}
+
+// max |g| over both force components (non-negative doubles order like their
+// bit patterns, so an unsigned 64-bit atomicMax suffices).  A non-finite
+// entry sets `bad`.
+__global__ void k_absmax(const double* gx, const double* gy, int64_t n,
+                         unsigned long long* out, unsigned int* bad);
+
+// F16S: multiply every stored deviation by `factor` (a power of two).
+__global__ void k_rescale_half(__half* h, int64_t count, float factor);
+
+// Launchers (defined per storage type).
+template <int S>
+struct Ops {
+    using T = typename StoreT<S>::T;
+    static cudaError_t step(const StepParams& a, const Coef<T>& c, int V, bool gen, bool check,
+                            cudaStream_t st);
+    static cudaError_t fields(const StepParams& a, const Coef<double>& c, T theta, double* out,
+                              cudaStream_t st);
+    static cudaError_t export_pop(const StepParams& a, T theta, double* out, cudaStream_t st);
+    static cudaError_t import_pop(const StepParams& a, T theta, const double* in, cudaStream_t st);
+};
+
+inline dim3 step_grid(int nx, int ny, int V) {
+    return dim3((unsigned)((nx + 32 * V - 1) / (32 * V)), (unsigned)((ny + BY - 1) / BY));
+}
+
+}  // namespace lbm

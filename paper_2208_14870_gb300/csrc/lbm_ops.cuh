@@ -1,0 +1,54 @@
+// lbm_ops.cuh -- launchers of the per-storage kernels; included by exactly one
+// translation unit per storage type (lbm_step_f64.cu, lbm_step_f32.cu,
+// lbm_step_f16s.cu), which instantiates Ops<S> for its type.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <int S>
+constexpr int max_vec() { return S == S_F64 ? 2 : 4; }
+
+template <int S, int V>
+static void launch_step_v(const StepParams& a, const Coef<typename StoreT<S>::T>& c, bool gen,
+                          bool check, cudaStream_t st) {
+    const dim3 block(32, BY);
+    const dim3 grid = step_grid(a.nx, a.ny, V);
+    if (gen) {
+        if (check) k_step<S, V, true, true><<<grid, block, 0, st>>>(a, c);
+        else k_step<S, V, true, false><<<grid, block, 0, st>>>(a, c);
+    } else {
+        if (check) k_step<S, V, false, true><<<grid, block, 0, st>>>(a, c);
+        else k_step<S, V, false, false><<<grid, block, 0, st>>>(a, c);
+    }
+}
+
+template <int S>
+cudaError_t Ops<S>::step(const StepParams& a, const Coef<T>& c, int V, bool gen, bool check,
+                         cudaStream_t st) {
+    if (V == 1) launch_step_v<S, 1>(a, c, gen, check, st);
+    else launch_step_v<S, max_vec<S>()>(a, c, gen, check, st);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t Ops<S>::fields(const StepParams& a, const Coef<double>& c, T theta, double* out,
+                           cudaStream_t st) {
+    k_fields<S><<<step_grid(a.nx, a.ny, 1), dim3(32, BY), 0, st>>>(a, c, theta, out);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t Ops<S>::export_pop(const StepParams& a, T theta, double* out, cudaStream_t st) {
+    k_export<S><<<step_grid(a.nx, a.ny, 1), dim3(32, BY), 0, st>>>(a, theta, out);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t Ops<S>::import_pop(const StepParams& a, T theta, const double* in, cudaStream_t st) {
+    k_import<S><<<step_grid(a.nx, a.ny, 1), dim3(32, BY), 0, st>>>(a, theta, in);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,333 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h``.
+
+Argument marshalling only: every step of the lattice Boltzmann path runs in
+the CUDA library ``_build/liblbm_gb300.so``.  There is no CPU fallback; if the
+library is missing the import of this module raises.
+
+Raw entry points keep the C names (``lbm_create``, ``lbm_iterate``, ...); they
+take plain ints / floats / addresses and raise ``LBMError`` on a negative
+status.  ``Lattice`` wraps one context with numpy / torch conveniences.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LBM_F64, LBM_F32, LBM_F16S = 0, 1, 2
+DTYPES = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S}
+
+LBM_OK = 0
+LBM_ERR_ARG = -1
+LBM_ERR_OOM = -2
+LBM_ERR_CUDA = -3
+LBM_ERR_DIVERGED = -4
+LBM_ERR_NOT_CONVERGED = -5
+LBM_ERR_TIMEOUT = -6
+LBM_ERR_STATE = -7
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA",
+                -4: "LBM_ERR_DIVERGED", -5: "LBM_ERR_NOT_CONVERGED", -6: "LBM_ERR_TIMEOUT",
+                -7: "LBM_ERR_STATE"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(status, "?"), status, message))
+        self.status = status
+
+
+class lbm_options(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("tau12", ctypes.c_double), ("tau22", ctypes.c_double)]
+
+
+class lbm_rates(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("w11", "ws", "wd", "w12", "w21", "w22", "theta")]
+
+
+_c = ctypes
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_SIGS = {
+    "lbm_create": (_c.c_int, [_c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_int, _c.POINTER(_vp)]),
+    "lbm_create_ex": (_c.c_int, [_c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_int,
+                                 _c.POINTER(lbm_options), _c.POINTER(_vp)]),
+    "lbm_destroy": (None, [_vp]),
+    "lbm_set_stream": (_c.c_int, [_vp, _vp]),
+    "lbm_set_force": (_c.c_int, [_vp, _vp, _vp]),
+    "lbm_set_force_device": (_c.c_int, [_vp, _vp, _vp]),
+    "lbm_reset": (_c.c_int, [_vp]),
+    "lbm_iterate": (_c.c_int, [_vp, _i64]),
+    "lbm_iterate_checked": (_c.c_int, [_vp, _i64, _c.c_int, _vp]),
+    "lbm_solve": (_c.c_int, [_vp, _c.c_double, _i64, _c.c_int, _c.POINTER(_i64),
+                             _c.POINTER(_c.c_double)]),
+    "lbm_get_displacement": (_c.c_int, [_vp, _vp, _vp]),
+    "lbm_get_stress": (_c.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_get_fields_device": (_c.c_int, [_vp, _vp]),
+    "lbm_get_populations": (_c.c_int, [_vp, _vp]),
+    "lbm_set_populations": (_c.c_int, [_vp, _vp]),
+    "lbm_get_step": (_c.c_int, [_vp, _c.POINTER(_i64)]),
+    "lbm_get_rates": (_c.c_int, [_vp, _c.POINTER(lbm_rates)]),
+    "lbm_get_device_bytes": (_c.c_int, [_vp, _c.POINTER(_c.c_size_t)]),
+    "lbm_last_error": (_c.c_char_p, []),
+    "lbm_version": (_c.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("CUDA library %s is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def last_error() -> str:
+    return _lib.lbm_last_error().decode()
+
+
+def _check(status: int, what: str) -> int:
+    if status != LBM_OK:
+        raise LBMError(status, "%s: %s" % (what, last_error()))
+    return status
+
+
+# ---------------------------------------------------------------------------
+# Raw entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def lbm_create(nx: int, ny: int, lam: float, mu: float, dtype: int) -> int:
+    out = _vp()
+    _check(_lib.lbm_create(nx, ny, lam, mu, dtype, ctypes.byref(out)), "lbm_create")
+    return out.value
+
+
+def lbm_create_ex(nx, ny, lam, mu, dtype, theta=0.0, tau12=0.0, tau22=0.0) -> int:
+    out = _vp()
+    opt = lbm_options(theta, tau12, tau22)
+    _check(_lib.lbm_create_ex(nx, ny, lam, mu, dtype, ctypes.byref(opt), ctypes.byref(out)),
+           "lbm_create_ex")
+    return out.value
+
+
+def lbm_destroy(ctx: int) -> None:
+    _lib.lbm_destroy(ctx)
+
+
+def lbm_set_stream(ctx: int, stream: int) -> None:
+    _check(_lib.lbm_set_stream(ctx, stream), "lbm_set_stream")
+
+
+def lbm_set_force(ctx: int, gx_ptr: int, gy_ptr: int) -> None:
+    _check(_lib.lbm_set_force(ctx, gx_ptr, gy_ptr), "lbm_set_force")
+
+
+def lbm_set_force_device(ctx: int, gx_ptr: int, gy_ptr: int) -> None:
+    _check(_lib.lbm_set_force_device(ctx, gx_ptr, gy_ptr), "lbm_set_force_device")
+
+
+def lbm_reset(ctx: int) -> None:
+    _check(_lib.lbm_reset(ctx), "lbm_reset")
+
+
+def lbm_iterate(ctx: int, n: int) -> None:
+    _check(_lib.lbm_iterate(ctx, n), "lbm_iterate")
+
+
+def lbm_iterate_checked(ctx: int, n: int, check_every: int, out_ptr: Optional[int] = None) -> None:
+    _check(_lib.lbm_iterate_checked(ctx, n, check_every, out_ptr), "lbm_iterate_checked")
+
+
+def lbm_solve(ctx: int, tol: float, max_iters: int, check_every: int):
+    """Returns (status, iters, residual); LBM_ERR_NOT_CONVERGED and
+    LBM_ERR_DIVERGED are returned, other errors raise."""
+    it = _i64()
+    r = ctypes.c_double()
+    st = _lib.lbm_solve(ctx, tol, max_iters, check_every, ctypes.byref(it), ctypes.byref(r))
+    if st not in (LBM_OK, LBM_ERR_NOT_CONVERGED, LBM_ERR_DIVERGED):
+        _check(st, "lbm_solve")
+    return st, it.value, r.value
+
+
+def lbm_get_displacement(ctx: int, ux_ptr: int, uy_ptr: int) -> None:
+    _check(_lib.lbm_get_displacement(ctx, ux_ptr, uy_ptr), "lbm_get_displacement")
+
+
+def lbm_get_stress(ctx: int, sxx_ptr: int, syy_ptr: int, sxy_ptr: int) -> None:
+    _check(_lib.lbm_get_stress(ctx, sxx_ptr, syy_ptr, sxy_ptr), "lbm_get_stress")
+
+
+def lbm_get_fields_device(ctx: int, out_ptr: int) -> None:
+    _check(_lib.lbm_get_fields_device(ctx, out_ptr), "lbm_get_fields_device")
+
+
+def lbm_get_populations(ctx: int, f_ptr: int) -> None:
+    _check(_lib.lbm_get_populations(ctx, f_ptr), "lbm_get_populations")
+
+
+def lbm_set_populations(ctx: int, f_ptr: int) -> None:
+    _check(_lib.lbm_set_populations(ctx, f_ptr), "lbm_set_populations")
+
+
+def lbm_get_step(ctx: int) -> int:
+    s = _i64()
+    _check(_lib.lbm_get_step(ctx, ctypes.byref(s)), "lbm_get_step")
+    return s.value
+
+
+def lbm_get_rates(ctx: int) -> dict:
+    r = lbm_rates()
+    _check(_lib.lbm_get_rates(ctx, ctypes.byref(r)), "lbm_get_rates")
+    return {k: getattr(r, k) for k, _ in lbm_rates._fields_}
+
+
+def lbm_get_device_bytes(ctx: int) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.lbm_get_device_bytes(ctx, ctypes.byref(b)), "lbm_get_device_bytes")
+    return b.value
+
+
+def lbm_version() -> str:
+    return _lib.lbm_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+def _host_f64(a: np.ndarray, n: int) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+class Lattice:
+    """One periodic lattice (context) on the current CUDA device."""
+
+    def __init__(self, nx: int, ny: int, lam: float, mu: float, dtype: str = "f32",
+                 theta: float = 0.0, tau12: float = 0.0, tau22: float = 0.0):
+        self.nx, self.ny, self.dtype = int(nx), int(ny), dtype
+        self.ctx = lbm_create_ex(self.nx, self.ny, float(lam), float(mu), DTYPES[dtype],
+                                 theta, tau12, tau22)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny
+
+    def set_stream(self, stream_handle: int):
+        lbm_set_stream(self.ctx, stream_handle)
+
+    def set_force(self, gx, gy):
+        """Host numpy arrays (copied) or device torch tensors (float64)."""
+        if hasattr(gx, "is_cuda") and gx.is_cuda:
+            assert gx.dtype == gy.dtype and str(gx.dtype) == "torch.float64"
+            assert gx.is_contiguous() and gy.is_contiguous() and gx.numel() == self.n
+            lbm_set_force_device(self.ctx, gx.data_ptr(), gy.data_ptr())
+            return
+        gxh, gyh = _host_f64(gx, self.n), _host_f64(gy, self.n)
+        lbm_set_force(self.ctx, gxh.ctypes.data, gyh.ctypes.data)
+
+    def reset(self):
+        lbm_reset(self.ctx)
+
+    def iterate(self, n: int):
+        lbm_iterate(self.ctx, int(n))
+
+    def iterate_checked(self, n: int, check_every: int) -> np.ndarray:
+        out = np.zeros(5, dtype=np.float64)
+        lbm_iterate_checked(self.ctx, int(n), int(check_every), out.ctypes.data)
+        return out
+
+    def solve(self, tol: float, max_iters: int = 10_000_000, check_every: int = 100):
+        return lbm_solve(self.ctx, float(tol), int(max_iters), int(check_every))
+
+    def displacement(self) -> np.ndarray:
+        out = np.empty((2, self.ny, self.nx), dtype=np.float64)
+        lbm_get_displacement(self.ctx, out[0].ctypes.data, out[1].ctypes.data)
+        return out
+
+    def stress(self) -> np.ndarray:
+        out = np.empty((3, self.ny, self.nx), dtype=np.float64)
+        lbm_get_stress(self.ctx, out[0].ctypes.data, out[1].ctypes.data, out[2].ctypes.data)
+        return out
+
+    def fields(self) -> np.ndarray:
+        """[u_x, u_y, sigma_xx, sigma_yy, sigma_xy] (lattice units), host FP64."""
+        return np.concatenate([self.displacement(), self.stress()])
+
+    def fields_device(self, out):
+        """Write the five fields into a contiguous CUDA float64 tensor of 5*n."""
+        assert out.is_cuda and out.is_contiguous() and out.numel() == 5 * self.n
+        lbm_get_fields_device(self.ctx, out.data_ptr())
+        return out
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((8, self.ny, self.nx), dtype=np.float64)
+        lbm_get_populations(self.ctx, out.ctypes.data)
+        return out
+
+    def set_populations(self, f: np.ndarray):
+        f = _host_f64(f, 8 * self.n)
+        lbm_set_populations(self.ctx, f.ctypes.data)
+
+    @property
+    def step(self) -> int:
+        return lbm_get_step(self.ctx)
+
+    @property
+    def rates(self) -> dict:
+        return lbm_get_rates(self.ctx)
+
+    @property
+    def device_bytes(self) -> int:
+        return lbm_get_device_bytes(self.ctx)
+
+
+def declared_functions(header: Optional[str] = None) -> list[str]:
+    """Names of the functions declared in include/*.h."""
+    import glob
+    import re
+    inc = os.path.dirname(header) if header else _build.INCLUDE
+    names = []
+    for h in sorted(glob.glob(os.path.join(inc, "*.h"))):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
