@@ -171,7 +171,7 @@ def workload_config(args):
             "nx": args.n, "ny": args.n, "iters_per_step": args.iters,
             "check_every": args.check_every, "E": 1.0, "nu": args.nu,
             "force": "16 modes, |kx|,|ky|<=8, amp N(0,1)/|k|^2, seed %#x" % FORCE_SEED,
-            "l2": "inputs larger than L2 (population state %.1f GB)" % (
+            "l2": "inputs larger than L2: %.1f GB of populations and force read+written per launch, L2 129 MB" % (
                 args.n * args.n * BYTES_PER_LUP[args.dtype] / 1e9)}
 
 

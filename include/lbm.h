@@ -35,9 +35,10 @@
  *  - Every call returns a status (LBM_OK = 0 or a negative LBM_ERR_*), never
  *    aborts, and leaves a human-readable message for lbm_last_error().
  *  - Work is enqueued on the context's stream (lbm_set_stream; default: the
- *    legacy default stream).  Calls that read or write host buffers, and
- *    lbm_solve, synchronise that stream before returning; lbm_iterate,
- *    lbm_reset, lbm_set_force_device and lbm_get_fields_device only enqueue.
+ *    legacy default stream).  Calls that read or write host buffers,
+ *    lbm_set_force_device and lbm_solve synchronise that stream before
+ *    returning; lbm_iterate, lbm_iterate_checked without output, lbm_reset and
+ *    lbm_get_fields_device only enqueue.
  *  - A context belongs to the device that was current at lbm_create and
  *    must be used from one host thread at a time.
  */
@@ -122,7 +123,9 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
  * the force magnitude rescales the stored deviations.  Synchronous. */
 int lbm_set_force(lbm_ctx *ctx, const double *gx, const double *gy);
 
-/* Same, from device arrays of nx*ny doubles.  Enqueued only. */
+/* Same, from device arrays of nx*ny doubles.  Synchronises the context's
+ * stream (the force is checked for non-finite values and, for LBM_F16S, its
+ * maximum sets the storage scale). */
 int lbm_set_force_device(lbm_ctx *ctx, const double *gx, const double *gy);
 
 /* Back to the zero state (Eq. init_cond with u_0 = 0); step counter 0; the
@@ -134,7 +137,11 @@ int lbm_reset(lbm_ctx *ctx);
 int lbm_iterate(lbm_ctx *ctx, int64_t n);
 
 /* n steps in which every check_every-th step also evaluates the steady-state
- * residual (fused into that step).  The last residual is written to
+ * residual (fused into that step).  A check fused into the step that takes
+ * the state from time t to t + 1 measures the displacement u^t of its input
+ * state; checks run in the steps with (t + 1) % check_every == 0, so the
+ * window between two checks is check_every steps.  The last residual is
+ * written to
  * out[0..4] if out is non-null: r_inf, r_2, max|u|, ||u||_2, nonfinite flag
  * (see lbm_solve).  Synchronous when out is non-null. */
 int lbm_iterate_checked(lbm_ctx *ctx, int64_t n, int check_every, double *out);

@@ -45,7 +45,7 @@ struct lbm_ctx {
     void* pop[2] = {nullptr, nullptr};
     float* car[2] = {nullptr, nullptr};
     void* force = nullptr;         // 2 planes of the storage force type
-    double* snap = nullptr;        // 2*n
+    void* snap = nullptr;          // 2*n of the snapshot type
     double* partials = nullptr;
     unsigned int* counter = nullptr;
     double* result = nullptr;      // kRes doubles (device)
@@ -58,11 +58,13 @@ struct lbm_ctx {
     int64_t step = 0;
     bool snap_valid = false;
     int64_t snap_step = 0;
-    int hexp = 0;
+    int hexp = 0;                  // F16S: stored deviation = deviation * 2^hexp
     float hscale = 1.0f, hinv = 1.0f;
+    double gmax = 0.0;             // max |g| of the current force
+    bool state_zero = true;        // state is the zero state (create / reset)
     int V = 1;
     size_t bytes = 0;
-    int64_t nblocks = 0;
+    int64_t nblocks = 0;           // grid of the persistent residual-check launch
 };
 
 namespace {
@@ -114,9 +116,9 @@ cudaError_t launch_step(lbm_ctx* c, bool check) {
     const StepParams a = params(c, c->cur);
     cudaError_t e;
     switch (c->dtype) {
-        case LBM_F64: e = Ops<S_F64>::step(a, coef<double>(c->rates), c->V, c->gen, check, c->stream); break;
-        case LBM_F32: e = Ops<S_F32>::step(a, coef<float>(c->rates), c->V, c->gen, check, c->stream); break;
-        default: e = Ops<S_F16S>::step(a, coef<float>(c->rates), c->V, c->gen, check, c->stream); break;
+        case LBM_F64: e = Ops<S_F64>::step(a, coef<double>(c->rates), c->V, c->gen, check, (int)c->nblocks, c->stream); break;
+        case LBM_F32: e = Ops<S_F32>::step(a, coef<float>(c->rates), c->V, c->gen, check, (int)c->nblocks, c->stream); break;
+        default: e = Ops<S_F16S>::step(a, coef<float>(c->rates), c->V, c->gen, check, (int)c->nblocks, c->stream); break;
     }
     if (e == cudaSuccess) {
         c->cur ^= 1;
@@ -179,6 +181,27 @@ void free_all(lbm_ctx* c) {
 // moments ~ tau * grad u ~ |g| * L / (2 pi); the scale maps |g| * L to 2^8,
 // leaving 2^7 of headroom below FP16's maximum and keeping values far above
 // its smallest normal.
+int half_exponent(const lbm_ctx* c, double gmax) {
+    const double L = double(c->nx > c->ny ? c->nx : c->ny);
+    int e = 8 - (int)std::ceil(std::log2(gmax * L));
+    return e < -60 ? -60 : (e > 60 ? 60 : e);
+}
+
+// Switch the FP16 scale to 2^e, rescaling the stored deviations if asked.
+int set_half_exponent(lbm_ctx* c, int e, bool rescale) {
+    if (e == c->hexp) return LBM_OK;
+    if (rescale) {
+        const float factor = std::ldexp(1.0f, e - c->hexp);
+        k_rescale_half<<<1024, 256, 0, c->stream>>>(static_cast<__half*>(c->pop[c->cur]),
+                                                   8 * c->plane, factor);
+        CK(cudaGetLastError());
+    }
+    c->hexp = e;
+    c->hscale = std::ldexp(1.0f, e);
+    c->hinv = std::ldexp(1.0f, -e);
+    return LBM_OK;
+}
+
 int update_half_scale(lbm_ctx* c, const double* gx_dev, const double* gy_dev) {
     CK(cudaMemsetAsync(c->absmax, 0, sizeof(unsigned long long), c->stream));
     CK(cudaMemsetAsync(c->bad, 0, sizeof(unsigned int), c->stream));
@@ -193,21 +216,13 @@ int update_half_scale(lbm_ctx* c, const double* gx_dev, const double* gy_dev) {
     unsigned int bad;
     std::memcpy(&bad, c->pinned + 1, sizeof(unsigned int));
     if (bad) return fail(LBM_ERR_ARG, "lbm_set_force: non-finite force");
+    c->gmax = gmax;
     if (c->dtype != LBM_F16S || gmax == 0.0) return LBM_OK;
-    const double L = double(c->nx > c->ny ? c->nx : c->ny);
-    int e = 8 - (int)std::ceil(std::log2(gmax * L));
-    if (e < -60) e = -60;
-    if (e > 60) e = 60;
-    if (e != c->hexp) {
-        const float factor = std::ldexp(1.0f, e - c->hexp);
-        k_rescale_half<<<1024, 256, 0, c->stream>>>(static_cast<__half*>(c->pop[c->cur]),
-                                                   8 * c->plane, factor);
-        CK(cudaGetLastError());
-        c->hexp = e;
-        c->hscale = std::ldexp(1.0f, e);
-        c->hinv = std::ldexp(1.0f, -e);
-    }
-    return LBM_OK;
+    int e = half_exponent(c, gmax);
+    // A non-zero state keeps its scale unless the new force asks for a
+    // smaller one: growing the stored values could overflow FP16.
+    if (!c->state_zero && e > c->hexp) e = c->hexp;
+    return set_half_exponent(c, e, !c->state_zero);
 }
 
 int set_force_dev(lbm_ctx* c, const double* gx, const double* gy) {
@@ -220,8 +235,8 @@ int set_force_dev(lbm_ctx* c, const double* gx, const double* gy) {
         k_force_convert<float><<<2048, 256, 0, c->stream>>>(gx, gy, fx, fx + c->plane, c->n);
         CK(cudaGetLastError());
     }
-    if (c->dtype == LBM_F16S) return update_half_scale(c, gx, gy);
-    return LBM_OK;
+    // validates the force (finite) for every storage type; picks the FP16 scale
+    return update_half_scale(c, gx, gy);
 }
 
 // Reads the residual of the last check; returns r_inf etc. in out[0..4].
@@ -305,8 +320,19 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     c->gen = !(c->rates.w12 == 1.0 && c->rates.w22 == 1.0);
     if (dtype == LBM_F64) c->V = nx >= 64 ? 2 : 1;
     else c->V = nx >= 128 ? 4 : 1;
-    const dim3 g = step_grid(nx, ny, c->V);
-    c->nblocks = (int64_t)g.x * g.y;
+    {
+        // persistent residual-check grid: resident blocks per SM x SMs
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        if (e != cudaSuccess || sms < 1) sms = 1;
+        int occ = dtype == LBM_F64 ? Ops<S_F64>::check_occupancy(c->V, c->gen)
+                : dtype == LBM_F32 ? Ops<S_F32>::check_occupancy(c->V, c->gen)
+                                   : Ops<S_F16S>::check_occupancy(c->V, c->gen);
+        const int64_t tiles = step_tiles(nx, ny, c->V);
+        c->nblocks = (int64_t)sms * occ;
+        if (c->nblocks > tiles) c->nblocks = tiles;
+        e = cudaSuccess;
+    }
 
     const size_t pb = pop_elem_bytes(dtype) * 8 * c->plane;
     const size_t fb = force_elem_bytes(dtype) * 2 * c->plane;
@@ -322,7 +348,8 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
         if (e == cudaSuccess && dtype == LBM_F16S) e = alloc((void**)&c->car[i], cb);
     }
     if (e == cudaSuccess) e = alloc(&c->force, fb);
-    if (e == cudaSuccess) e = alloc((void**)&c->snap, sizeof(double) * 2 * c->n);
+    const size_t snap_bytes = (dtype == LBM_F64 ? sizeof(double) : sizeof(float)) * 2 * c->n;
+    if (e == cudaSuccess) e = alloc(&c->snap, snap_bytes);
     if (e == cudaSuccess) e = alloc((void**)&c->partials, sizeof(double) * kRes * c->nblocks);
     if (e == cudaSuccess) e = alloc((void**)&c->counter, sizeof(unsigned int));
     if (e == cudaSuccess) e = alloc((void**)&c->result, sizeof(double) * kRes);
@@ -334,7 +361,7 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     if (e == cudaSuccess && dtype == LBM_F16S) e = cudaMemset(c->car[0], 0, cb);
     if (e == cudaSuccess && dtype == LBM_F16S) e = cudaMemset(c->car[1], 0, cb);
     if (e == cudaSuccess) e = cudaMemset(c->force, 0, fb);
-    if (e == cudaSuccess) e = cudaMemset(c->snap, 0, sizeof(double) * 2 * c->n);
+    if (e == cudaSuccess) e = cudaMemset(c->snap, 0, snap_bytes);
     if (e == cudaSuccess) e = cudaMemset(c->counter, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -398,6 +425,11 @@ int lbm_reset(lbm_ctx* c) {
         CK(cudaMemsetAsync(c->car[c->cur], 0, sizeof(float) * 2 * c->plane, c->stream));
     c->step = 0;
     c->snap_valid = false;
+    c->state_zero = true;
+    if (c->dtype == LBM_F16S && c->gmax > 0.0) {
+        rc = set_half_exponent(c, half_exponent(c, c->gmax), false);
+        if (rc) return rc;
+    }
     return LBM_OK;
 }
 
@@ -405,6 +437,7 @@ int lbm_iterate(lbm_ctx* c, int64_t n) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (n < 0) return fail(LBM_ERR_ARG, "lbm_iterate: n must be >= 0");
+    if (n > 0) c->state_zero = false;
     for (int64_t i = 0; i < n; ++i) {
         cudaError_t e = launch_step(c, false);
         if (e != cudaSuccess) return cuda_fail(e, "lbm_iterate: step launch");
@@ -416,6 +449,7 @@ int lbm_iterate_checked(lbm_ctx* c, int64_t n, int check_every, double* out) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (n < 0 || check_every < 1) return fail(LBM_ERR_ARG, "lbm_iterate_checked: bad n or check_every");
+    if (n > 0) c->state_zero = false;
     int64_t last_window = 0;
     bool any = false;
     for (int64_t i = 0; i < n; ++i) {
@@ -448,6 +482,7 @@ int lbm_solve(lbm_ctx* c, double tol, int64_t max_iters, int check_every, int64_
     if (rc) return rc;
     if (!(tol >= 0.0) || max_iters < 0 || check_every < 1)
         return fail(LBM_ERR_ARG, "lbm_solve: bad tol, max_iters or check_every");
+    if (max_iters > 0) c->state_zero = false;
     int64_t done = 0;
     double r = INFINITY;
     int status = LBM_ERR_NOT_CONVERGED;
@@ -552,8 +587,20 @@ int lbm_set_populations(lbm_ctx* c, const double* f) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!f) return fail(LBM_ERR_ARG, "lbm_set_populations: null pointer");
-    for (int64_t i = 0; i < 8 * c->n; ++i)
+    double fmax_abs = 0.0;
+    for (int64_t i = 0; i < 8 * c->n; ++i) {
         if (!std::isfinite(f[i])) return fail(LBM_ERR_ARG, "lbm_set_populations: non-finite value");
+        fmax_abs = std::fmax(fmax_abs, std::fabs(f[i]));
+    }
+    if (c->dtype == LBM_F16S && fmax_abs > 0.0) {
+        // deviations are bounded by a few times max|f|; keep them below 2^12
+        int e = 10 - (int)std::ceil(std::log2(fmax_abs));
+        if (c->gmax > 0.0 && half_exponent(c, c->gmax) < e) e = half_exponent(c, c->gmax);
+        if (e > 60) e = 60;
+        if (e < -60) e = -60;
+        rc = set_half_exponent(c, e, false);
+        if (rc) return rc;
+    }
     rc = ensure_staging(c, 8 * c->n);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->staging, f, 8 * c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -568,6 +615,7 @@ int lbm_set_populations(lbm_ctx* c, const double* f) {
     CK(cudaStreamSynchronize(c->stream));
     c->step = 0;
     c->snap_valid = false;
+    c->state_zero = false;
     return LBM_OK;
 }
 

@@ -26,9 +26,11 @@ constexpr int kThreads = 32 * BY;
 enum Storage { S_F64 = 0, S_F32 = 1, S_F16S = 2 };
 
 template <int S> struct StoreT;
-template <> struct StoreT<S_F64> { using T = double; using P = double; using G = double; };
-template <> struct StoreT<S_F32> { using T = float; using P = float; using G = float; };
-template <> struct StoreT<S_F16S> { using T = float; using P = __half; using G = float; };
+// T: collision arithmetic, P: stored population, G: stored force,
+// U: displacement snapshot of the residual check (the type u is computed in).
+template <> struct StoreT<S_F64> { using T = double; using P = double; using G = double; using U = double; };
+template <> struct StoreT<S_F32> { using T = float; using P = float; using G = float; using U = float; };
+template <> struct StoreT<S_F16S> { using T = float; using P = __half; using G = float; using U = float; };
 
 // Residual partial sums of one block: max|du|, max|u|, sum du^2, sum u^2,
 // non-finite flag.
@@ -45,7 +47,7 @@ struct StepParams {
     const void* gy;
     float hscale;           // F16S: stored = deviation * hscale (power of two)
     float hinv;             // 1 / hscale
-    double* snap;           // residual: u_x, u_y snapshot, 2 planes of nx*ny FP64
+    void* snap;             // residual: u_x, u_y snapshot, 2 planes of nx*ny (type U)
     double* partials;       // residual: kRes doubles per block
     unsigned int* counter;  // residual: blocks finished (reset by the last block)
     double* result;         // residual: kRes doubles
@@ -118,10 +120,15 @@ __device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
     }
 }
 
-// Block-wide reduction of the residual partials followed by the grid-level
-// pass: the last block to finish (counted with an atomic) reduces all block
-// partials and writes the result, then resets the counter for the next check.
-__device__ __forceinline__ void residual_reduce(const StepParams& a, double v[kRes]) {
+// Residual reduction.  Each thread holds partials over its V nodes in the
+// snapshot type U (max|du|, max|u|, sum du^2, sum u^2, non-finite flag); a
+// warp combines them in U (maxima are exact; FP32 sums of at most 32*V terms
+// carry a relative error below 1e-6), then the block and the grid combine
+// the warp results in FP64.  The grid-level pass is done by the last block to
+// finish (counted with an atomic), which also resets the counter for the next
+// check.
+template <typename U>
+__device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) {
     __shared__ double sh[kRes][kThreads / 32];
     __shared__ bool is_last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -129,34 +136,30 @@ __device__ __forceinline__ void residual_reduce(const StepParams& a, double v[kR
     const int nwarps = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
-        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[0] = max(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = max(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
         v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
         v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
-        v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], o));
+        v[4] = max(v[4], __shfl_xor_sync(0xffffffffu, v[4], o));
     }
     if (lane == 0)
-        for (int k = 0; k < kRes; ++k) sh[k][warp] = v[k];
+        for (int k = 0; k < kRes; ++k) sh[k][warp] = double(v[k]);
     __syncthreads();
     const unsigned int nblocks = gridDim.x * gridDim.y;
     const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
-    if (warp == 0) {
-        double w[kRes];
-        for (int k = 0; k < kRes; ++k) w[k] = (lane < nwarps) ? sh[k][lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            w[0] = fmax(w[0], __shfl_xor_sync(0xffffffffu, w[0], o));
-            w[1] = fmax(w[1], __shfl_xor_sync(0xffffffffu, w[1], o));
-            w[2] += __shfl_xor_sync(0xffffffffu, w[2], o);
-            w[3] += __shfl_xor_sync(0xffffffffu, w[3], o);
-            w[4] = fmax(w[4], __shfl_xor_sync(0xffffffffu, w[4], o));
+    if (tid == 0) {
+        double w[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < nwarps; ++i) {
+            w[0] = fmax(w[0], sh[0][i]);
+            w[1] = fmax(w[1], sh[1][i]);
+            w[2] += sh[2][i];
+            w[3] += sh[3][i];
+            w[4] = fmax(w[4], sh[4][i]);
         }
-        if (lane == 0) {
-            for (int k = 0; k < kRes; ++k) a.partials[(int64_t)bid * kRes + k] = w[k];
-            __threadfence();
-            const unsigned int done = atomicAdd(a.counter, 1u);
-            is_last = (done == nblocks - 1);
-        }
+        for (int k = 0; k < kRes; ++k) a.partials[(int64_t)bid * kRes + k] = w[k];
+        __threadfence();
+        const unsigned int done = atomicAdd(a.counter, 1u);
+        is_last = (done == nblocks - 1);
     }
     __syncthreads();
     if (!is_last) return;
@@ -197,26 +200,40 @@ __device__ __forceinline__ void residual_reduce(const StepParams& a, double v[kR
     }
 }
 
-// One pseudo-time step (Algorithm 1) over the whole lattice.  CHECK adds the
-// steady-state residual: u^n is compared with the snapshot u^(n-k), the
-// snapshot is overwritten with u^n, and max/L2 partials are reduced in FP64.
+// One pseudo-time step (Algorithm 1) over the whole lattice.
+//
+// The lattice is cut into tiles of 32*V columns by BY rows; block b handles
+// tiles b, b + gridDim.x, ...  The plain step is launched with one block per
+// tile.  CHECK adds the steady-state residual and is launched as a persistent
+// grid (a few blocks per SM): u^t (the displacement of this step's input
+// state) is compared with the snapshot taken at the previous check, the
+// snapshot is overwritten with u^t, and each block reduces its partials once,
+// after all of its tiles (FP64 across warps, blocks and the grid).
 template <int S, int V, bool GEN, bool CHECK>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, CHECK ? 2 : (S == S_F32 ? 4 : 3))
 k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
     using T = typename StoreT<S>::T;
     using G = typename StoreT<S>::G;
+    using U = typename StoreT<S>::U;
     const int nx = a.nx, ny = a.ny;
-    const int y = blockIdx.y * BY + threadIdx.y;
-    const int xb = blockIdx.x * (32 * V) + threadIdx.x;
-    double acc[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (y < ny) {
+    const int ntx = (nx + 32 * V - 1) / (32 * V);
+    const int64_t ntiles = (int64_t)ntx * ((ny + BY - 1) / BY);
+    const G* __restrict__ gxp = static_cast<const G*>(a.gx);
+    const G* __restrict__ gyp = static_cast<const G*>(a.gy);
+    U* __restrict__ snap = static_cast<U*>(a.snap);
+    const int64_t n = (int64_t)nx * ny;
+    U acc[kRes] = {U(0), U(0), U(0), U(0), U(0)};
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
+        const int y = ty * BY + threadIdx.y;
+        const int xb = tx * (32 * V) + threadIdx.x;
+        if (y >= ny) continue;
         const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
         const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
-        const G* __restrict__ gxp = static_cast<const G*>(a.gx);
-        const G* __restrict__ gyp = static_cast<const G*>(a.gy);
         // Phase 1: issue every load of the thread's V nodes before any store,
-        // so that up to V*10 loads are in flight per thread.
+        // so that up to V*10 (V*12 with the snapshot) loads are in flight.
         T f[V][8], gx[V], gy[V];
+        U so[V][2];
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             const int x = xb + 32 * j;
@@ -224,6 +241,10 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
                 gather<S>(a, r0, rm, rp, x, wrap_dec(x, nx), wrap_inc(x, nx), f[j], c.theta);
                 gx[j] = T(ldg(gxp + r0 + x));
                 gy[j] = T(ldg(gyp + r0 + x));
+                if (CHECK) {
+                    so[j][0] = snap[r0 + x];
+                    so[j][1] = snap[n + r0 + x];
+                }
             }
         }
         // Phase 2: collide and store.
@@ -236,22 +257,20 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
                 const Mom<T> s = collide<T, GEN>(moments(f[j]), gx[j], gy[j], c, u, v);
                 scatter_local<S>(a, idx, s, c.theta);
                 if (CHECK) {
-                    const double ud = double(u), vd = double(v);
-                    const int64_t n = (int64_t)nx * ny;
-                    const double uo = a.snap[idx], vo = a.snap[n + idx];
-                    a.snap[idx] = ud;
-                    a.snap[n + idx] = vd;
-                    const double du = ud - uo, dv = vd - vo;
-                    acc[0] = fmax(acc[0], fmax(fabs(du), fabs(dv)));
-                    acc[1] = fmax(acc[1], fmax(fabs(ud), fabs(vd)));
+                    const U uu = U(u), vv = U(v);
+                    snap[idx] = uu;
+                    snap[n + idx] = vv;
+                    const U du = uu - so[j][0], dv = vv - so[j][1];
+                    acc[0] = max(acc[0], max(abs(du), abs(dv)));
+                    acc[1] = max(acc[1], max(abs(uu), abs(vv)));
                     acc[2] += du * du + dv * dv;
-                    acc[3] += ud * ud + vd * vd;
-                    if (!(isfinite(ud) && isfinite(vd))) acc[4] = 1.0;
+                    acc[3] += uu * uu + vv * vv;
+                    if (!(isfinite(uu) && isfinite(vv))) acc[4] = U(1);
                 }
             }
         }
     }
-    if (CHECK) residual_reduce(a, acc);
+    if (CHECK) residual_reduce<U>(a, acc);
 }
 
 // Solution fields of the current state (Table 2, Eq. compute_bared), FP64:
@@ -365,13 +384,20 @@ __global__ void k_rescale_half(__half* h, int64_t count, float factor);
 template <int S>
 struct Ops {
     using T = typename StoreT<S>::T;
+    // check_blocks: grid of the persistent CHECK launch (<= partials slots)
     static cudaError_t step(const StepParams& a, const Coef<T>& c, int V, bool gen, bool check,
-                            cudaStream_t st);
+                            int check_blocks, cudaStream_t st);
+    // resident blocks per SM of the CHECK kernel
+    static int check_occupancy(int V, bool gen);
     static cudaError_t fields(const StepParams& a, const Coef<double>& c, T theta, double* out,
                               cudaStream_t st);
     static cudaError_t export_pop(const StepParams& a, T theta, double* out, cudaStream_t st);
     static cudaError_t import_pop(const StepParams& a, T theta, const double* in, cudaStream_t st);
 };
+
+inline int64_t step_tiles(int nx, int ny, int V) {
+    return (int64_t)((nx + 32 * V - 1) / (32 * V)) * ((ny + BY - 1) / BY);
+}
 
 inline dim3 step_grid(int nx, int ny, int V) {
     return dim3((unsigned)((nx + 32 * V - 1) / (32 * V)), (unsigned)((ny + BY - 1) / BY));

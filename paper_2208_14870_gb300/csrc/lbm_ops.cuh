@@ -12,9 +12,11 @@ constexpr int max_vec() { return S == S_F64 ? 2 : 4; }
 
 template <int S, int V>
 static void launch_step_v(const StepParams& a, const Coef<typename StoreT<S>::T>& c, bool gen,
-                          bool check, cudaStream_t st) {
+                          bool check, int check_blocks, cudaStream_t st) {
     const dim3 block(32, BY);
-    const dim3 grid = step_grid(a.nx, a.ny, V);
+    const int64_t tiles = step_tiles(a.nx, a.ny, V);
+    const unsigned int grid = (unsigned int)(check ? (tiles < check_blocks ? tiles : check_blocks)
+                                                   : tiles);
     if (gen) {
         if (check) k_step<S, V, true, true><<<grid, block, 0, st>>>(a, c);
         else k_step<S, V, true, false><<<grid, block, 0, st>>>(a, c);
@@ -26,10 +28,23 @@ static void launch_step_v(const StepParams& a, const Coef<typename StoreT<S>::T>
 
 template <int S>
 cudaError_t Ops<S>::step(const StepParams& a, const Coef<T>& c, int V, bool gen, bool check,
-                         cudaStream_t st) {
-    if (V == 1) launch_step_v<S, 1>(a, c, gen, check, st);
-    else launch_step_v<S, max_vec<S>()>(a, c, gen, check, st);
+                         int check_blocks, cudaStream_t st) {
+    if (V == 1) launch_step_v<S, 1>(a, c, gen, check, check_blocks, st);
+    else launch_step_v<S, max_vec<S>()>(a, c, gen, check, check_blocks, st);
     return cudaGetLastError();
+}
+
+template <int S, int V>
+static int occ_v(bool gen) {
+    int b = 0;
+    if (gen) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S, V, true, true>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S, V, false, true>, kThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+template <int S>
+int Ops<S>::check_occupancy(int V, bool gen) {
+    return V == 1 ? occ_v<S, 1>(gen) : occ_v<S, max_vec<S>()>(gen);
 }
 
 template <int S>

@@ -167,22 +167,26 @@ def test_rectangular_random_force_steady_state_f64():
 
 
 def test_residual_definition_matches_oracle():
+    """Checks every k = 10 steps well before steady state (slow k = 1 mode)."""
     lam, mu = W.lame_2d(1.0, 0.3)
     rates = oracle.relaxation_rates(lam, mu)
-    nx, ny = 40, 24
-    pw = W.random_force(nx, ny, 4, 3, seed=4)
-    gx, gy = W.random_force_grid(pw)
+    nx, ny = 64, 48
+    man = W.sinusoid(nx, 1, lam, mu, ny=ny)
+    gx, gy = man.force()
     with Lattice(nx, ny, lam, mu, "f64") as lat:
         lat.set_force(gx, gy)
-        out = lat.iterate_checked(300, 100)     # checks at 100, 200, 300
-    f200 = oracle.run(oracle.zero_state(nx, ny), gx, gy, rates, 200)
-    f300 = oracle.run(f200, gx, gy, rates, 100)
-    u200 = oracle.fields(f200, gx, gy, rates)[:2]
-    u300 = oracle.fields(f300, gx, gy, rates)[:2]
-    r_inf, r_2 = oracle.residual(u300, u200, 100)
+        # checks fused into steps 10, 20, 30 measure u at their input times
+        # 9, 19, 29; the last residual compares u^29 with u^19
+        out = lat.iterate_checked(30, 10)
+    f20 = oracle.run(oracle.zero_state(nx, ny), gx, gy, rates, 19)
+    f30 = oracle.run(f20, gx, gy, rates, 10)
+    u20 = oracle.fields(f20, gx, gy, rates)[:2]
+    u30 = oracle.fields(f30, gx, gy, rates)[:2]
+    r_inf, r_2 = oracle.residual(u30, u20, 10)
+    assert r_inf > 1e-4
     assert abs(out[0] - r_inf) < 1e-12 * r_inf
     assert abs(out[1] - r_2) < 1e-12 * r_2
-    assert abs(out[2] - np.max(np.abs(u300))) < 1e-14
+    assert abs(out[2] - np.max(np.abs(u30))) < 1e-14 * np.max(np.abs(u30))
     assert out[4] == 0.0
 
 
@@ -245,8 +249,10 @@ def test_reset_restores_zero_state():
 
 
 def test_f16s_force_rescale_keeps_state():
-    """Changing the force magnitude rescales the stored FP16 deviations
-    without changing the represented populations (power-of-two factor)."""
+    """Changing the force magnitude rescales the stored FP16 deviations by a
+    power of two: exact when the scale grows (force made smaller); when it
+    shrinks, the smallest deviations lose bits as they move toward FP16's
+    subnormal range."""
     lam, mu = W.lame_2d(1.0, 0.3)
     nx, ny = 64, 48
     pw = W.random_force(nx, ny, 4, 3, seed=21)
@@ -255,9 +261,10 @@ def test_f16s_force_rescale_keeps_state():
         lat.set_force(gx, gy)
         lat.iterate(40)
         before = lat.populations()
+        lat.set_force(gx / 1024.0, gy / 1024.0)
+        assert np.array_equal(lat.populations(), before)
         lat.set_force(gx * 1024.0, gy * 1024.0)
-        after = lat.populations()
-        assert rel(after, before) < 1e-6
+        assert rel(lat.populations(), before) < 1e-4
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16s"])
