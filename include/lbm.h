@@ -189,6 +189,56 @@ int lbm_get_device_bytes(lbm_ctx *ctx, size_t *bytes);
 /* Message of the last failing call on this host thread ("" if none). */
 const char *lbm_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free residual-checked step.  The paper has no counterpart: this
+ * is a service of the library for callers that may not allocate device
+ * memory -- plug-ins whose host application owns every device byte through
+ * its own pool, and latency-critical loops that cannot afford cudaMalloc /
+ * cudaFree, which may synchronise the whole device.
+ *
+ * One pseudo-time step with the fused steady-state residual (the kernel of
+ * lbm_iterate_checked) on buffers the caller owns.  No memory is allocated:
+ * the residual reduction's scratch (one slot of partial sums per block plus a
+ * completion counter, about 40 KB) is a static device array of the library,
+ * held by every GPU that loads the library until the process exits.
+ *
+ *  dtype     LBM_F64 or LBM_F32 (LBM_F16S is not supported here).
+ *  lambda,mu Lame parameters as in lbm_create; standard theta = 1/3 and
+ *            w_12 = w_21 = w_22 = 1.
+ *  f_src     device, 8 planes of nx*ny values of the storage type, plane
+ *            stride nx*ny, population order of this header: the stored state,
+ *            i.e. the post-collision populations f*_i(x) of the previous step
+ *            (all zeros is the zero state of Eq. init_cond).
+ *  f_dst     device, same layout, receives the state after the step; must not
+ *            alias f_src.
+ *  gx, gy    device, nx*ny values of the storage type (lattice force).
+ *  snapshot  device, 2 planes of nx*ny values of the storage type: u_x, u_y
+ *            of the previous check on input (zeros before the first); on
+ *            output the displacement of this step's input state.
+ *  result    device, 5 doubles: max|du|, max|u|, sum du^2, sum u^2 and a
+ *            non-finite flag, du being the change of u since the snapshot;
+ *            r_inf = result[0] / (k * result[1]) for a window of k steps.
+ *  grid_blocks  blocks of the launch, 0 = one per resident slot of the device
+ *            (capped at LBM_NOALLOC_MAX_BLOCKS and at the number of tiles).
+ *  stream    cudaStream_t (null: legacy default stream).  Enqueued only.
+ *
+ * Returns LBM_OK; LBM_ERR_ARG for nx or ny < 1, nx*ny > 2^31, another dtype,
+ * non-finite or non-positive moduli, a null or aliased buffer, or
+ * grid_blocks outside [0, LBM_NOALLOC_MAX_BLOCKS] (more blocks than the static
+ * scratch has slots); LBM_ERR_CUDA if a CUDA call fails.  No message is left
+ * for lbm_last_error.
+ *
+ * The first call on each device looks up the device address of the static
+ * scratch (with that device current); make that first call before any stream
+ * capture.  All calls share the one scratch array and it keeps the last
+ * call's contents; each call clears the counter before its launch.  Calls
+ * whose launches overlap on the GPU (different streams, or several host
+ * threads) race on the scratch and give wrong residuals: serialise them. */
+#define LBM_NOALLOC_MAX_BLOCKS 1024
+int lbm_step_checked_noalloc(int nx, int ny, double lambda, double mu, int dtype,
+                             const void *f_src, void *f_dst, const void *gx, const void *gy,
+                             void *snapshot, double *result, int grid_blocks, void *stream);
+
 /* Library version string. */
 const char *lbm_version(void);
 

@@ -73,6 +73,8 @@ _SIGS = {
     "lbm_get_rates": (_c.c_int, [_vp, _c.POINTER(lbm_rates)]),
     "lbm_get_device_bytes": (_c.c_int, [_vp, _c.POINTER(_c.c_size_t)]),
     "lbm_last_error": (_c.c_char_p, []),
+    "lbm_step_checked_noalloc": (_c.c_int, [_c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_int,
+                                            _vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp]),
     "lbm_version": (_c.c_char_p, []),
 }
 
@@ -204,6 +206,23 @@ def lbm_get_device_bytes(ctx: int) -> int:
     b = ctypes.c_size_t()
     _check(_lib.lbm_get_device_bytes(ctx, ctypes.byref(b)), "lbm_get_device_bytes")
     return b.value
+
+
+LBM_NOALLOC_MAX_BLOCKS = 1024
+
+
+def lbm_step_checked_noalloc(nx: int, ny: int, lam: float, mu: float, dtype: int, f_src: int,
+                             f_dst: int, gx: int, gy: int, snapshot: int, result: int,
+                             grid_blocks: int = 0, stream: int = 0) -> None:
+    """One residual-checked step on caller-owned device buffers; allocates
+    nothing (see include/lbm.h).  Raises LBMError on a rejected call."""
+    st = _lib.lbm_step_checked_noalloc(nx, ny, lam, mu, dtype, f_src, f_dst, gx, gy, snapshot,
+                                       result, grid_blocks, stream)
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_step_checked_noalloc rejected the call (needs LBM_F64 or "
+                           "LBM_F32, 1 <= nx, ny, nx*ny <= 2^31, mu > 0, lambda + mu > 0, "
+                           "non-null distinct buffers, 0 <= grid_blocks <= %d)"
+                       % LBM_NOALLOC_MAX_BLOCKS)
 
 
 def lbm_version() -> str:
