@@ -190,6 +190,53 @@ int lbm_get_device_bytes(lbm_ctx *ctx, size_t *bytes);
 const char *lbm_last_error(void);
 
 /* ---------------------------------------------------------------------------
+ * Batched solves.  Many independent periodic problems (each the setting of
+ * Sec. 2 with its own size, Lame parameters and body force) are solved in one
+ * packed device arena by a persistent cooperative kernel: every step walks the
+ * tiles of all running problems, a grid-wide barrier separates steps, and the
+ * residual check of Sec. 2.1 (reading of lbm_solve) is fused into the last step
+ * of each chunk of check_every steps, per problem.  Converged problems drop
+ * out of the tile list between chunks.  The chunk (accumulator reset, kernel,
+ * read-back) is replayed from a CUDA graph.  The tile width (32, 64 or 128
+ * columns) is chosen by an autotuner that times the first three chunks and
+ * caches the choice per workload signature in $LBM_AUTOTUNE_CACHE (default
+ * ~/.cache/lbm_gb300/autotune.txt; LBM_AUTOTUNE=0 ignores the cache).
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_problem {
+    int nx, ny;                 /* lattice size, >= 1 */
+    double lambda, mu;          /* Lame parameters, lattice units; theta = 1/3,
+                                   w_12 = w_21 = w_22 = 1 */
+    const double *gx, *gy;      /* host, nx*ny each: body force (copied) */
+} lbm_problem;
+
+typedef struct lbm_result {
+    int status;                 /* LBM_OK, LBM_ERR_NOT_CONVERGED or LBM_ERR_DIVERGED */
+    int64_t iters;              /* steps taken (a multiple of check_every) */
+    double residual;            /* last r_inf of the problem */
+    double *ux, *uy;            /* host outputs, nx*ny each, caller-owned; may be null */
+    double *sxx, *syy, *sxy;    /* host outputs (lattice-unit stress); may be null */
+} lbm_result;
+
+typedef struct lbm_batch_report {
+    int tile_v;                 /* tile width used, in warps of 32 columns */
+    int blocks;                 /* persistent grid size */
+    int64_t chunks;             /* chunk launches */
+    int64_t lattice_updates;    /* sum over problems of nodes x steps */
+    double device_ms;           /* device time of the chunks (CUDA events) */
+    double wall_ms;             /* whole call */
+} lbm_batch_report;
+
+/* Solve `count` problems to residual tol (checked every check_every >= 2
+ * steps; a problem stops at the first check below tol, at divergence, or at
+ * the first check at or beyond max_iters steps).  dtype: LBM_F32 or LBM_F16S.
+ * results[i] receives status, steps, residual and, where the pointers are
+ * non-null, the FP64 displacement and stress (Table 2).  report may be null.
+ * Synchronous.  Returns LBM_OK when every problem was run (per-problem
+ * outcomes are in results), LBM_ERR_ARG / LBM_ERR_OOM / LBM_ERR_CUDA otherwise. */
+int lbm_batch_solve(int count, const lbm_problem *probs, int dtype, double tol, int check_every,
+                    int64_t max_iters, lbm_result *results, lbm_batch_report *report);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free residual-checked step.  The paper has no counterpart: this
  * is a service of the library for callers that may not allocate device
  * memory -- plug-ins whose host application owns every device byte through

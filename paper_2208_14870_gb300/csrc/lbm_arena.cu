@@ -1,0 +1,146 @@
+// lbm_arena.cu -- the persistent chunk kernel of the packed lattice arena
+// (see lbm_arena.cuh), one instantiation per storage type (FP32, FP16-shifted)
+// and tile width.
+#include "lbm_arena.cuh"
+
+namespace lbm {
+
+namespace cg = cooperative_groups;
+
+template <int S, int V, bool CHECK>
+__device__ __forceinline__ void arena_tile(const BatchArgs& A, const BatchProb& P, int tile,
+                                           int s, float acc[kRes]) {
+    StepParams a{};
+    const int64_t n = (int64_t)P.nx * P.ny;
+    a.nx = P.nx;
+    a.ny = P.ny;
+    a.plane = n;
+    const int src = (P.parity + s) & 1;
+    char* ps = src ? A.pop1 : A.pop0;
+    char* pd = src ? A.pop0 : A.pop1;
+    a.src = ps + P.pop_off;
+    a.dst = pd + P.pop_off;
+    if (S == S_F16S) {
+        char* cs = src ? A.car1 : A.car0;
+        char* cd = src ? A.car0 : A.car1;
+        a.csrc = reinterpret_cast<const float*>(cs + P.car_off);
+        a.cdst = reinterpret_cast<float*>(cd + P.car_off);
+        a.hscale = P.hscale;
+        a.hinv = P.hinv;
+    }
+    float* fsb = reinterpret_cast<float*>(A.fs + P.fs_off);
+    a.gx = fsb;
+    a.gy = fsb + n;
+    a.snap = fsb + 2 * n;
+    Coef<float> c{};
+    c.a11 = P.a11;
+    c.as = P.as;
+    c.ad = P.ad;
+    c.theta = P.theta;
+    const int ntx = (P.nx + 32 * V - 1) / (32 * V);
+    const int ty = tile / ntx, tx = tile - ty * ntx;
+    step_tile<S, V, false, CHECK>(a, c, tx, ty, acc);
+}
+
+// Block reduction of one tile's residual partials into the problem's FP64
+// accumulator (maxima through the bit patterns of non-negative doubles).
+__device__ __forceinline__ void tile_to_problem(float acc[kRes], double* dst,
+                                                float (&red)[kRes][kThreads / 32]) {
+    const int tid = threadIdx.y * 32 + threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc[0] = fmaxf(acc[0], __shfl_xor_sync(0xffffffffu, acc[0], o));
+        acc[1] = fmaxf(acc[1], __shfl_xor_sync(0xffffffffu, acc[1], o));
+        acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
+        acc[3] += __shfl_xor_sync(0xffffffffu, acc[3], o);
+        acc[4] = fmaxf(acc[4], __shfl_xor_sync(0xffffffffu, acc[4], o));
+    }
+    if (lane == 0)
+        for (int k = 0; k < kRes; ++k) red[k][warp] = acc[k];
+    __syncthreads();
+    if (tid == 0) {
+        double m0 = 0.0, m1 = 0.0, s2 = 0.0, s3 = 0.0, b = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            m0 = fmax(m0, (double)red[0][w]);
+            m1 = fmax(m1, (double)red[1][w]);
+            s2 += (double)red[2][w];
+            s3 += (double)red[3][w];
+            b = fmax(b, (double)red[4][w]);
+        }
+        unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+        atomicMax(d + 0, (unsigned long long)__double_as_longlong(m0));
+        atomicMax(d + 1, (unsigned long long)__double_as_longlong(m1));
+        atomicAdd(dst + 2, s2);
+        atomicAdd(dst + 3, s3);
+        atomicMax(d + 4, (unsigned long long)__double_as_longlong(b));
+    }
+    __syncthreads();
+}
+
+template <int S, int V>
+__global__ void __launch_bounds__(kThreads, 2) k_arena_chunk(const BatchArgs A) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ float red[kRes][kThreads / 32];
+    const int ntiles = *A.ntiles;
+    for (int s = 0; s < A.nsteps; ++s) {
+        const bool check = (s == A.nsteps - 1);
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const uint2 tl = A.tiles[t];
+            const BatchProb P = A.probs[tl.x];
+            float acc[kRes] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            if (!check) {
+                arena_tile<S, V, false>(A, P, (int)tl.y, s, acc);
+            } else {
+                arena_tile<S, V, true>(A, P, (int)tl.y, s, acc);
+                tile_to_problem(acc, A.acc + (int64_t)tl.x * kRes, red);
+            }
+        }
+        if (s + 1 < A.nsteps) grid.sync();
+    }
+}
+
+template <int S, int V>
+static cudaError_t launch_v(const BatchArgs& a, int grid, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(32, BY);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_arena_chunk<S, V>, a);
+}
+
+cudaError_t launch_arena_chunk(int dtype, int V, const BatchArgs& a, int grid, cudaStream_t st) {
+    if (dtype == S_F16S) {
+        switch (V) {
+            case 1: return launch_v<S_F16S, 1>(a, grid, st);
+            case 2: return launch_v<S_F16S, 2>(a, grid, st);
+            case 4: return launch_v<S_F16S, 4>(a, grid, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (V) {
+        case 1: return launch_v<S_F32, 1>(a, grid, st);
+        case 2: return launch_v<S_F32, 2>(a, grid, st);
+        case 4: return launch_v<S_F32, 4>(a, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int S, int V>
+static int occ() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_arena_chunk<S, V>, kThreads, 0);
+    return b;
+}
+
+int arena_occupancy(int dtype, int V) {
+    if (dtype == S_F16S) return V == 1 ? occ<S_F16S, 1>() : V == 2 ? occ<S_F16S, 2>() : occ<S_F16S, 4>();
+    return V == 1 ? occ<S_F32, 1>() : V == 2 ? occ<S_F32, 2>() : occ<S_F32, 4>();
+}
+
+}  // namespace lbm

@@ -1,0 +1,110 @@
+// lbm_arena.cuh -- packed lattice arena for many independent periodic
+// problems of uneven sizes and material parameters, advanced together by one
+// persistent cooperative kernel per chunk of k steps.
+//
+// Every problem p owns, in three device buffers,
+//   pop[0], pop[1] : its 8 population planes (ping-pong; FP32 or FP16),
+//   car[0], car[1] : FP16-shifted only: the two FP32 carrier planes,
+//   fs             : force (2 planes) then residual snapshot (2 planes), FP32,
+// placed by a first-fit allocator (256-byte aligned).  The work of one step
+// is the list of (problem, tile) pairs of the active problems; the kernel
+// walks that list grid-stride, then synchronises the whole grid before the
+// next step (cooperative launch).  The last step of each chunk carries the
+// residual check; its per-problem partial sums go to per-problem FP64
+// accumulators with atomics.  The host reads them after the chunk, retires
+// converged problems, admits new ones and rebuilds the tile list between
+// chunks; the chunk itself (accumulator reset, kernel, accumulator read-back)
+// is replayed from a CUDA graph.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+struct BatchProb {
+    int64_t pop_off;   // bytes into each population buffer
+    int64_t car_off;   // bytes into each carrier buffer (F16S)
+    int64_t fs_off;    // bytes into the force/snapshot buffer
+    int nx, ny, ntx, dtype, parity;
+    float a11, as, ad, theta, hscale, hinv;
+};
+
+struct BatchArgs {
+    const BatchProb* probs;
+    const uint2* tiles;        // (problem, tile)
+    const int* ntiles;         // device scalar: number of valid tiles
+    char* pop0;
+    char* pop1;
+    char* car0;
+    char* car1;
+    char* fs;
+    double* acc;               // kRes doubles per problem
+    int nsteps;
+};
+
+constexpr int kArenaAlign = 256;
+
+// First-fit allocator over [0, capacity) with coalescing of free ranges.
+class RangeAllocator {
+public:
+    void reset(int64_t capacity) {
+        free_.clear();
+        if (capacity > 0) free_[0] = capacity;
+        cap_ = capacity;
+    }
+    int64_t capacity() const { return cap_; }
+    // returns offset or -1
+    int64_t alloc(int64_t bytes) {
+        bytes = (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const int64_t off = it->first, rest = it->second - bytes;
+                free_.erase(it);
+                if (rest > 0) free_[off + bytes] = rest;
+                return off;
+            }
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t bytes) {
+        bytes = (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    int64_t largest_free() const {
+        int64_t m = 0;
+        for (auto& kv : free_) m = kv.second > m ? kv.second : m;
+        return m;
+    }
+
+private:
+    std::map<int64_t, int64_t> free_;
+    int64_t cap_ = 0;
+};
+
+// Launch one chunk: nsteps steps of every listed tile (all of storage type
+// dtype: S_F32 or S_F16S), residual check fused into the last step.  Tile
+// width 32*V, V in {1, 2, 4}.  Cooperative launch: grid must not exceed
+// arena_occupancy(dtype, V) x SM count.
+cudaError_t launch_arena_chunk(int dtype, int V, const BatchArgs& a, int grid, cudaStream_t st);
+// Resident blocks per SM of the chunk kernel.
+int arena_occupancy(int dtype, int V);
+
+}  // namespace lbm

@@ -35,6 +35,15 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 }  // namespace
 
+// Shared with the batched and serving modules: the message lbm_last_error()
+// returns on this host thread.
+namespace lbm {
+int set_last_error(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+}  // namespace lbm
+
 struct lbm_ctx {
     int device = 0;
     int nx = 0, ny = 0, dtype = 0;
@@ -176,16 +185,8 @@ void free_all(lbm_ctx* c) {
     if (c->pinned) cudaFreeHost(c->pinned);
 }
 
-// FP16-shifted storage: pick the power-of-two scale of the stored deviations
-// from the force magnitude.  At steady state the deviations are second
-// moments ~ tau * grad u ~ |g| * L / (2 pi); the scale maps |g| * L to 2^8,
-// leaving 2^7 of headroom below FP16's maximum and keeping values far above
-// its smallest normal.
-int half_exponent(const lbm_ctx* c, double gmax) {
-    const double L = double(c->nx > c->ny ? c->nx : c->ny);
-    int e = 8 - (int)std::ceil(std::log2(gmax * L));
-    return e < -60 ? -60 : (e > 60 ? 60 : e);
-}
+// FP16-shifted storage: scale exponent from the force (f16s_exponent).
+int half_exponent(const lbm_ctx* c, double gmax) { return f16s_exponent(gmax, c->nx, c->ny); }
 
 // Switch the FP16 scale to 2^e, rescaling the stored deviations if asked.
 int set_half_exponent(lbm_ctx* c, int e, bool rescale) {

@@ -1,0 +1,491 @@
+// lbm_engine.cu -- host side of the packed lattice arena (lbm_engine.cuh).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <sys/stat.h>
+
+#include "../../include/lbm.h"
+#include "lbm_engine.cuh"
+
+namespace lbm {
+
+namespace {
+
+int cuerr(cudaError_t e, const char* what, std::string* err) {
+    if (err) *err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+#define ECK(call)                                                 \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuerr(e_, #call, err);      \
+    } while (0)
+
+int64_t pop_bytes_per_node(int dtype) { return dtype == S_F16S ? 8 * 2 : 8 * 4; }
+int64_t car_bytes_per_node(int dtype) { return dtype == S_F16S ? 2 * 4 : 0; }
+constexpr int64_t kFsBytesPerNode = 4 * 4;  // force (2) + snapshot (2), FP32
+
+}  // namespace
+
+ArenaEngine::~ArenaEngine() {
+    if (st_) cudaStreamSynchronize(st_);
+    for (auto& g : graph_)
+        if (g) cudaGraphExecDestroy(g);
+    for (int i = 0; i < 2; ++i) {
+        if (pop_[i]) cudaFree(pop_[i]);
+        if (car_[i]) cudaFree(car_[i]);
+    }
+    if (fs_) cudaFree(fs_);
+    if (d_probs_) cudaFree(d_probs_);
+    if (d_acc_) cudaFree(d_acc_);
+    if (d_tiles_) cudaFree(d_tiles_);
+    if (d_ntiles_) cudaFree(d_ntiles_);
+    if (d_fields_) cudaFree(d_fields_);
+    if (h_acc_) cudaFreeHost(h_acc_);
+    if (h_tiles_) cudaFreeHost(h_tiles_);
+    if (h_force_) cudaFreeHost(h_force_);
+    if (ev0_) cudaEventDestroy(ev0_);
+    if (ev1_) cudaEventDestroy(ev1_);
+}
+
+int64_t ArenaEngine::bytes_for(int64_t n) const {
+    auto al = [](int64_t b) { return (b + kArenaAlign - 1) / kArenaAlign * kArenaAlign; };
+    return 2 * al(pop_bytes_per_node(dtype_) * n) + 2 * al(car_bytes_per_node(dtype_) * n) +
+           al(kFsBytesPerNode * n);
+}
+
+int ArenaEngine::init(int dtype, int64_t node_capacity, int max_probs, int check_every,
+                      cudaStream_t st, std::string* err) {
+    if (dtype != S_F32 && dtype != S_F16S) {
+        if (err) *err = "arena: storage must be LBM_F32 or LBM_F16S";
+        return LBM_ERR_ARG;
+    }
+    dtype_ = dtype;
+    k_ = check_every;
+    st_ = st;
+    int dev = 0;
+    ECK(cudaGetDevice(&dev));
+    ECK(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t slack = (int64_t)max_probs * kArenaAlign;
+    const int64_t pb = pop_bytes_per_node(dtype) * node_capacity + slack;
+    const int64_t cb = car_bytes_per_node(dtype) * node_capacity + slack;
+    const int64_t fb = kFsBytesPerNode * node_capacity + slack;
+    for (int i = 0; i < 2; ++i) {
+        ECK(cudaMalloc(&pop_[i], pb));
+        dev_bytes_ += pb;
+        if (dtype == S_F16S) {
+            ECK(cudaMalloc(&car_[i], cb));
+            dev_bytes_ += cb;
+        }
+    }
+    ECK(cudaMalloc(&fs_, fb));
+    dev_bytes_ += fb;
+    apop_.reset(pb);
+    acar_.reset(dtype == S_F16S ? cb : 0);
+    afs_.reset(fb);
+    probs_.assign(max_probs, HostProb());
+    ECK(cudaMalloc(&d_probs_, sizeof(BatchProb) * max_probs));
+    ECK(cudaMalloc(&d_acc_, sizeof(double) * kRes * max_probs));
+    ECK(cudaMallocHost(&h_acc_, sizeof(double) * kRes * max_probs));
+    ECK(cudaMalloc(&d_ntiles_, sizeof(int)));
+    ECK(cudaMemsetAsync(d_ntiles_, 0, sizeof(int), st_));
+    ECK(cudaEventCreate(&ev0_));
+    ECK(cudaEventCreate(&ev1_));
+    dev_bytes_ += sizeof(BatchProb) * max_probs + sizeof(double) * kRes * max_probs;
+    return LBM_OK;
+}
+
+int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* gx, const double* gy,
+                       double tol, int64_t max_iters, std::string* err) {
+    if (nx < 1 || ny < 1 || !gx || !gy || !(mu > 0.0) || !(lambda + mu > 0.0) ||
+        !std::isfinite(lambda) || !std::isfinite(mu)) {
+        if (err) *err = "admit: bad problem (sizes, moduli or null force)";
+        return LBM_ERR_ARG;
+    }
+    int slot = -1;
+    for (int i = 0; i < (int)probs_.size(); ++i)
+        if (probs_[i].state == P_FREE) {
+            slot = i;
+            break;
+        }
+    if (slot < 0) return -1;
+    const int64_t n = (int64_t)nx * ny;
+    HostProb p;
+    p.pop_bytes = pop_bytes_per_node(dtype_) * n;
+    p.car_bytes = car_bytes_per_node(dtype_) * n;
+    p.fs_bytes = kFsBytesPerNode * n;
+    p.pop_off = apop_.alloc(p.pop_bytes);
+    if (p.pop_off < 0) return -1;
+    if (dtype_ == S_F16S) {
+        p.car_off = acar_.alloc(p.car_bytes);
+        if (p.car_off < 0) {
+            apop_.release(p.pop_off, p.pop_bytes);
+            return -1;
+        }
+    } else {
+        p.car_off = 0;
+    }
+    p.fs_off = afs_.alloc(p.fs_bytes);
+    if (p.fs_off < 0) {
+        apop_.release(p.pop_off, p.pop_bytes);
+        if (dtype_ == S_F16S) acar_.release(p.car_off, p.car_bytes);
+        return -1;
+    }
+    // force -> FP32 staging (pinned), with the FP16 scale from its maximum
+    if (h_force_cap_ < 2 * n) {
+        if (h_force_) {
+            ECK(cudaStreamSynchronize(st_));
+            cudaFreeHost(h_force_);
+            h_force_ = nullptr;
+        }
+        ECK(cudaMallocHost(&h_force_, sizeof(float) * 2 * n));
+        h_force_cap_ = 2 * n;
+    }
+    ECK(cudaStreamSynchronize(st_));  // the staging may still feed a previous copy
+    double gmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double a = gx[i], b = gy[i];
+        if (!std::isfinite(a) || !std::isfinite(b)) {
+            apop_.release(p.pop_off, p.pop_bytes);
+            if (dtype_ == S_F16S) acar_.release(p.car_off, p.car_bytes);
+            afs_.release(p.fs_off, p.fs_bytes);
+            if (err) *err = "admit: non-finite force";
+            return LBM_ERR_ARG;
+        }
+        gmax = std::fmax(gmax, std::fmax(std::fabs(a), std::fabs(b)));
+        h_force_[i] = (float)a;
+        h_force_[n + i] = (float)b;
+    }
+    ECK(cudaMemcpyAsync(fs_ + p.fs_off, h_force_, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, st_));
+    ECK(cudaMemsetAsync(fs_ + p.fs_off + sizeof(float) * 2 * n, 0, sizeof(float) * 2 * n, st_));
+    ECK(cudaMemsetAsync(pop_[0] + p.pop_off, 0, p.pop_bytes, st_));
+    if (dtype_ == S_F16S) ECK(cudaMemsetAsync(car_[0] + p.car_off, 0, p.car_bytes, st_));
+    p.parity = 0;
+    p.nx = nx;
+    p.ny = ny;
+    p.n = n;
+    p.lambda = lambda;
+    p.mu = mu;
+    // Table 1 / Eq. relaxation_rate with theta = 1/3, w_12 = w_21 = w_22 = 1
+    const double theta = 1.0 / 3.0, K = lambda + mu;
+    p.theta = (float)theta;
+    p.a11 = (float)(1.0 - 1.0 / (mu / theta + 0.5));
+    p.as = (float)(1.0 - 1.0 / (2.0 * K / (1.0 + theta) + 0.5));
+    p.ad = (float)(1.0 - 1.0 / (2.0 * mu / (1.0 - theta) + 0.5));
+    p.hexp = dtype_ == S_F16S ? f16s_exponent(gmax, nx, ny) : 0;
+    p.tol = tol;
+    p.max_iters = max_iters;
+    p.state = P_RUNNING;
+    probs_[slot] = p;
+    ++nrunning_;
+    tiles_dirty_ = true;
+    desc_dirty_ = true;
+    return slot;
+}
+
+int64_t ArenaEngine::running_tiles(int V) const {
+    int64_t t = 0;
+    for (const auto& p : probs_)
+        if (p.state == P_RUNNING) t += step_tiles(p.nx, p.ny, V);
+    return t;
+}
+
+int64_t ArenaEngine::running_nodes() const {
+    int64_t t = 0;
+    for (const auto& p : probs_)
+        if (p.state == P_RUNNING) t += p.n;
+    return t;
+}
+
+int ArenaEngine::grid_blocks(int V) const { return arena_occupancy(dtype_, V) * sms_; }
+
+int64_t ArenaEngine::free_nodes_hint() const {
+    return apop_.largest_free() / pop_bytes_per_node(dtype_);
+}
+
+int ArenaEngine::upload_tiles(int V, std::string* err) {
+    const int64_t nt = running_tiles(V);
+    if (nt > (int64_t)INT32_MAX) {
+        if (err) *err = "arena: too many tiles";
+        return LBM_ERR_ARG;
+    }
+    if (h_tiles_cap_ < nt) {
+        if (h_tiles_) {
+            ECK(cudaStreamSynchronize(st_));
+            cudaFreeHost(h_tiles_);
+        }
+        h_tiles_cap_ = nt + nt / 4 + 1024;
+        ECK(cudaMallocHost(&h_tiles_, sizeof(uint2) * h_tiles_cap_));
+    }
+    if (tiles_cap_ < nt) {
+        if (d_tiles_) {
+            ECK(cudaStreamSynchronize(st_));
+            cudaFree(d_tiles_);
+        }
+        tiles_cap_ = nt + nt / 4 + 1024;
+        ECK(cudaMalloc(&d_tiles_, sizeof(uint2) * tiles_cap_));
+        for (auto& g : graph_)  // the graphs hold the old tile pointer
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+    ECK(cudaStreamSynchronize(st_));  // the pinned list may feed a previous copy
+    int64_t t = 0;
+    for (int s = 0; s < (int)probs_.size(); ++s) {
+        const HostProb& p = probs_[s];
+        if (p.state != P_RUNNING) continue;
+        const int64_t m = step_tiles(p.nx, p.ny, V);
+        for (int64_t i = 0; i < m; ++i) h_tiles_[t++] = make_uint2((unsigned)s, (unsigned)i);
+    }
+    static thread_local int nt_host;
+    nt_host = (int)nt;
+    if (nt > 0) ECK(cudaMemcpyAsync(d_tiles_, h_tiles_, sizeof(uint2) * nt, cudaMemcpyHostToDevice, st_));
+    ECK(cudaMemcpyAsync(d_ntiles_, &nt_host, sizeof(int), cudaMemcpyHostToDevice, st_));
+    ECK(cudaStreamSynchronize(st_));
+    tiles_V_ = V;
+    tiles_dirty_ = false;
+    return LBM_OK;
+}
+
+int ArenaEngine::ensure_graph(int V, std::string* err) {
+    if (graph_[V] || graph_failed_[V]) return LBM_OK;
+    BatchArgs a{};
+    a.probs = d_probs_;
+    a.tiles = d_tiles_;
+    a.ntiles = d_ntiles_;
+    a.pop0 = pop_[0];
+    a.pop1 = pop_[1];
+    a.car0 = car_[0];
+    a.car1 = car_[1];
+    a.fs = fs_;
+    a.acc = d_acc_;
+    a.nsteps = k_;
+    const int grid = grid_blocks(V);
+    if (grid < 1) {
+        if (err) *err = "arena: chunk kernel cannot be resident";
+        return LBM_ERR_CUDA;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(d_acc_, 0, sizeof(double) * kRes * probs_.size(), st_);
+        launch_arena_chunk(dtype_, V, a, grid, st_);
+        cudaMemcpyAsync(h_acc_, d_acc_, sizeof(double) * kRes * probs_.size(), cudaMemcpyDeviceToHost, st_);
+        e = cudaStreamEndCapture(st_, &g);
+    }
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&graph_[V], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear; fall back to direct launches
+        graph_[V] = nullptr;
+        graph_failed_[V] = true;
+    }
+    return LBM_OK;
+}
+
+int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
+    if (V != 1 && V != 2 && V != 4) {
+        if (err) *err = "arena: tile width must be 1, 2 or 4 warps of 32";
+        return LBM_ERR_ARG;
+    }
+    if (device_ms) *device_ms = 0.0f;
+    if (nrunning_ == 0) return LBM_OK;
+    if (tiles_dirty_ || tiles_V_ != V) {
+        int rc = upload_tiles(V, err);
+        if (rc) return rc;
+    }
+    if (desc_dirty_) {
+        std::vector<BatchProb> d(probs_.size());
+        for (size_t i = 0; i < probs_.size(); ++i) {
+            const HostProb& p = probs_[i];
+            BatchProb& b = d[i];
+            b.pop_off = p.pop_off;
+            b.car_off = p.car_off;
+            b.fs_off = p.fs_off;
+            b.nx = p.nx;
+            b.ny = p.ny;
+            b.ntx = 0;
+            b.dtype = dtype_;
+            b.parity = p.parity;
+            b.a11 = p.a11;
+            b.as = p.as;
+            b.ad = p.ad;
+            b.theta = p.theta;
+            b.hscale = std::ldexp(1.0f, p.hexp);
+            b.hinv = std::ldexp(1.0f, -p.hexp);
+        }
+        ECK(cudaMemcpyAsync(d_probs_, d.data(), sizeof(BatchProb) * d.size(), cudaMemcpyHostToDevice, st_));
+        ECK(cudaStreamSynchronize(st_));
+        desc_dirty_ = false;
+    }
+    int rc = ensure_graph(V, err);
+    if (rc) return rc;
+    ECK(cudaEventRecord(ev0_, st_));
+    if (graph_[V]) {
+        ECK(cudaGraphLaunch(graph_[V], st_));
+    } else {
+        BatchArgs a{};
+        a.probs = d_probs_;
+        a.tiles = d_tiles_;
+        a.ntiles = d_ntiles_;
+        a.pop0 = pop_[0];
+        a.pop1 = pop_[1];
+        a.car0 = car_[0];
+        a.car1 = car_[1];
+        a.fs = fs_;
+        a.acc = d_acc_;
+        a.nsteps = k_;
+        ECK(cudaMemsetAsync(d_acc_, 0, sizeof(double) * kRes * probs_.size(), st_));
+        ECK(launch_arena_chunk(dtype_, V, a, grid_blocks(V), st_));
+        ECK(cudaMemcpyAsync(h_acc_, d_acc_, sizeof(double) * kRes * probs_.size(), cudaMemcpyDeviceToHost, st_));
+    }
+    ECK(cudaEventRecord(ev1_, st_));
+    ECK(cudaStreamSynchronize(st_));
+    if (device_ms) ECK(cudaEventElapsedTime(device_ms, ev0_, ev1_));
+    for (int s = 0; s < (int)probs_.size(); ++s) {
+        HostProb& p = probs_[s];
+        if (p.state != P_RUNNING) continue;
+        p.steps += k_;
+        p.lups += p.n * k_;
+        if (k_ & 1) {
+            p.parity ^= 1;
+            desc_dirty_ = true;
+        }
+        const double* raw = h_acc_ + (int64_t)s * kRes;
+        bool done = false;
+        if (raw[4] != 0.0 || !std::isfinite(raw[0]) || !std::isfinite(raw[1])) {
+            p.status = LBM_ERR_DIVERGED;
+            p.residual = INFINITY;
+            done = true;
+        } else if (!p.snap_valid) {
+            p.snap_valid = true;
+            p.residual = INFINITY;
+        } else {
+            p.residual = raw[1] > 0.0 ? raw[0] / ((double)k_ * raw[1]) : 0.0;
+            if (p.residual < p.tol) {
+                p.status = LBM_OK;
+                done = true;
+            }
+        }
+        if (!done && p.steps >= p.max_iters) {
+            p.status = LBM_ERR_NOT_CONVERGED;
+            done = true;
+        }
+        if (done) {
+            p.state = P_DONE;
+            --nrunning_;
+            tiles_dirty_ = true;
+        }
+    }
+    return LBM_OK;
+}
+
+int ArenaEngine::recover(int slot, double* ux, double* uy, double* sxx, double* syy, double* sxy,
+                         std::string* err) {
+    const HostProb& p = probs_[slot];
+    if (p.state == P_FREE) {
+        if (err) *err = "recover: empty slot";
+        return LBM_ERR_STATE;
+    }
+    if (d_fields_cap_ < 5 * p.n) {
+        if (d_fields_) {
+            ECK(cudaStreamSynchronize(st_));
+            cudaFree(d_fields_);
+        }
+        ECK(cudaMalloc(&d_fields_, sizeof(double) * 5 * p.n));
+        d_fields_cap_ = 5 * p.n;
+    }
+    StepParams a{};
+    a.nx = p.nx;
+    a.ny = p.ny;
+    a.plane = p.n;
+    a.src = pop_[p.parity] + p.pop_off;
+    a.dst = pop_[p.parity ^ 1] + p.pop_off;
+    if (dtype_ == S_F16S) {
+        a.csrc = reinterpret_cast<const float*>(car_[p.parity] + p.car_off);
+        a.cdst = reinterpret_cast<float*>(car_[p.parity ^ 1] + p.car_off);
+        a.hscale = std::ldexp(1.0f, p.hexp);
+        a.hinv = std::ldexp(1.0f, -p.hexp);
+    }
+    float* fsb = reinterpret_cast<float*>(fs_ + p.fs_off);
+    a.gx = fsb;
+    a.gy = fsb + p.n;
+    a.snap = fsb + 2 * p.n;
+    const double theta = 1.0 / 3.0, K = p.lambda + p.mu;
+    const double w11 = 1.0 / (p.mu / theta + 0.5), ws = 1.0 / (2.0 * K / (1.0 + theta) + 0.5),
+                 wd = 1.0 / (2.0 * p.mu / (1.0 - theta) + 0.5);
+    Coef<double> c{};
+    c.b11 = 1.0 - 0.5 * w11;
+    c.bs = 1.0 - 0.5 * ws;
+    c.bd = 1.0 - 0.5 * wd;
+    c.theta = theta;
+    cudaError_t e = dtype_ == S_F16S ? Ops<S_F16S>::fields(a, c, (float)theta, d_fields_, st_)
+                                     : Ops<S_F32>::fields(a, c, (float)theta, d_fields_, st_);
+    ECK(e);
+    double* outs[5] = {ux, uy, sxx, syy, sxy};
+    for (int i = 0; i < 5; ++i)
+        if (outs[i])
+            ECK(cudaMemcpyAsync(outs[i], d_fields_ + i * p.n, sizeof(double) * p.n,
+                                cudaMemcpyDeviceToHost, st_));
+    ECK(cudaStreamSynchronize(st_));
+    return LBM_OK;
+}
+
+void ArenaEngine::release(int slot) {
+    HostProb& p = probs_[slot];
+    if (p.state == P_FREE) return;
+    if (p.state == P_RUNNING) {
+        --nrunning_;
+        tiles_dirty_ = true;
+    }
+    apop_.release(p.pop_off, p.pop_bytes);
+    if (dtype_ == S_F16S) acar_.release(p.car_off, p.car_bytes);
+    afs_.release(p.fs_off, p.fs_bytes);
+    p = HostProb();
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner cache: "key V" lines in $LBM_AUTOTUNE_CACHE (default
+// $HOME/.cache/lbm_gb300/autotune.txt).  LBM_AUTOTUNE=0 disables lookups.
+// ---------------------------------------------------------------------------
+
+namespace {
+std::mutex g_tune_mutex;
+
+std::string cache_path() {
+    const char* p = std::getenv("LBM_AUTOTUNE_CACHE");
+    if (p && *p) return p;
+    const char* h = std::getenv("HOME");
+    std::string dir = std::string(h && *h ? h : "/tmp") + "/.cache";
+    mkdir(dir.c_str(), 0755);
+    dir += "/lbm_gb300";
+    mkdir(dir.c_str(), 0755);
+    return dir + "/autotune.txt";
+}
+}  // namespace
+
+int autotune_lookup(const std::string& key) {
+    const char* off = std::getenv("LBM_AUTOTUNE");
+    if (off && std::string(off) == "0") return 0;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    std::ifstream in(cache_path());
+    std::string k;
+    int v = 0, found = 0;
+    while (in >> k >> v)
+        if (k == key) found = v;
+    return found;
+}
+
+void autotune_store(const std::string& key, int V) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    std::ofstream out(cache_path(), std::ios::app);
+    if (out) out << key << " " << V << "\n";
+}
+
+}  // namespace lbm

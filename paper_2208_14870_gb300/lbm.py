@@ -350,3 +350,64 @@ def declared_functions(header: Optional[str] = None) -> list[str]:
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
         names += re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", txt)
     return sorted(set(names))
+
+
+# ---------------------------------------------------------------------------
+# Batched solves (lbm_batch_solve)
+# ---------------------------------------------------------------------------
+
+class lbm_problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("lam", ctypes.c_double),
+                ("mu", ctypes.c_double), ("gx", _vp), ("gy", _vp)]
+
+
+class lbm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int64), ("residual", ctypes.c_double),
+                ("ux", _vp), ("uy", _vp), ("sxx", _vp), ("syy", _vp), ("sxy", _vp)]
+
+
+class lbm_batch_report(ctypes.Structure):
+    _fields_ = [("tile_v", ctypes.c_int), ("blocks", ctypes.c_int), ("chunks", ctypes.c_int64),
+                ("lattice_updates", ctypes.c_int64), ("device_ms", ctypes.c_double),
+                ("wall_ms", ctypes.c_double)]
+
+
+_lib.lbm_batch_solve.restype = ctypes.c_int
+_lib.lbm_batch_solve.argtypes = [ctypes.c_int, ctypes.POINTER(lbm_problem), ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_int64,
+                                 ctypes.POINTER(lbm_result), ctypes.POINTER(lbm_batch_report)]
+
+
+def batch_solve(problems, dtype: str = "f32", tol: float = 1e-8, check_every: int = 100,
+                max_iters: int = 10_000_000, fields: bool = True):
+    """Solve many problems in one arena.  ``problems``: iterable of
+    (nx, ny, lam, mu, gx, gy) with host FP64 arrays.  Returns (results, report):
+    results is a list of dicts (status, iters, residual[, fields (5, ny, nx)])."""
+    problems = list(problems)
+    cnt = len(problems)
+    arr = (lbm_problem * cnt)()
+    res = (lbm_result * cnt)()
+    keep = []
+    outs = []
+    for i, (nx, ny, lam, mu, gx, gy) in enumerate(problems):
+        gxh = _host_f64(gx, nx * ny)
+        gyh = _host_f64(gy, nx * ny)
+        keep += [gxh, gyh]
+        arr[i] = lbm_problem(nx, ny, lam, mu, gxh.ctypes.data, gyh.ctypes.data)
+        if fields:
+            o = np.empty((5, ny, nx), dtype=np.float64)
+            outs.append(o)
+            res[i].ux, res[i].uy, res[i].sxx, res[i].syy, res[i].sxy = [o[c].ctypes.data for c in range(5)]
+        else:
+            outs.append(None)
+    rep = lbm_batch_report()
+    _check(_lib.lbm_batch_solve(cnt, arr, DTYPES[dtype], tol, check_every, max_iters, res,
+                                ctypes.byref(rep)), "lbm_batch_solve")
+    results = []
+    for i in range(cnt):
+        d = {"status": res[i].status, "iters": res[i].iters, "residual": res[i].residual}
+        if fields:
+            d["fields"] = outs[i]
+        results.append(d)
+    report = {k: getattr(rep, k) for k, _ in lbm_batch_report._fields_}
+    return results, report

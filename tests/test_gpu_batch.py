@@ -1,0 +1,106 @@
+"""Batched solves in one packed arena (lbm_batch_solve) against the
+single-lattice path and against the oracle's exact fixed points."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.fourier as F
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2208_14870_gb300 as P  # noqa: E402
+
+
+@pytest.fixture(autouse=True)
+def _tune_cache(tmp_path, monkeypatch):
+    monkeypatch.setenv("LBM_AUTOTUNE_CACHE", str(tmp_path / "autotune.txt"))
+
+
+def rel_per_field(a, b):
+    return max(float(np.max(np.abs(a[i] - b[i]))) / max(float(np.max(np.abs(b[i]))), 1e-300)
+               for i in range(a.shape[0]))
+
+
+SIZES = [(33, 17), (64, 64), (130, 7), (40, 96), (1, 9), (200, 150), (77, 77), (16, 300),
+         (128, 128), (5, 5), (250, 31), (96, 40)]
+
+
+def make_problems(sizes, seed=0):
+    probs = []
+    rng = W.SplitMix64(seed)
+    for i, (nx, ny) in enumerate(sizes):
+        nu = 0.45 * rng.uniform()
+        lam, mu = W.lame_2d(1.0, nu)
+        pw = W.random_force(nx, ny, 4, 3, seed=1000 + i)
+        gx, gy = W.random_force_grid(pw)
+        probs.append((nx, ny, lam, mu, gx, gy, pw))
+    return probs
+
+
+@pytest.mark.parametrize("dtype,tol_fix", [("f32", 2e-5), ("f16s", 2e-3)])
+def test_batch_matches_single_lattice_and_fixed_point(dtype, tol_fix):
+    probs = make_problems(SIZES)
+    k = 50
+    results, report = P.batch_solve([p[:6] for p in probs], dtype=dtype, tol=1e-7 if dtype == "f32" else 1e-6,
+                                    check_every=k, max_iters=2_000_000)
+    assert report["tile_v"] in (1, 2, 4) and report["chunks"] >= 3
+    for (nx, ny, lam, mu, gx, gy, pw), r in zip(probs, results):
+        assert r["status"] == P.LBM_OK, (nx, ny, r)
+        rates = oracle.relaxation_rates(lam, mu)
+        ks, fh, flh = F.steady_state_modes(nx, ny, pw.modes(), rates)
+        X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
+        exact = np.stack([F.evaluate_modes(ks, flh[:, c], X, Y) for c in range(5)])
+        err = rel_per_field(r["fields"], exact)
+        assert err < tol_fix, (nx, ny, err)
+        # the single-lattice path with the same checks stops at the same step
+        with P.Lattice(nx, ny, lam, mu, dtype) as lat:
+            lat.set_force(gx, gy)
+            st, iters, res = lat.solve(1e-7 if dtype == "f32" else 1e-6, 2_000_000, k)
+            assert st == P.LBM_OK
+            assert abs(iters - r["iters"]) <= k
+            # same arithmetic, but the compiler may contract a*b+c into FMAs
+            # differently in the two kernels: agreement to the storage tolerance
+            assert rel_per_field(r["fields"], lat.fields()) < tol_fix
+
+
+def test_batch_reports_divergence_and_iteration_cap():
+    ok = make_problems([(48, 40), (64, 32)], seed=3)
+    # nu = -0.4, E~ = 0.082 is outside the stable region (Sec. 6.3.5)
+    lam_u, mu_u = W.lame_2d(0.082, -0.4)
+    pw = W.random_force(32, 32, 4, 3, seed=9)
+    gx, gy = W.random_force_grid(pw)
+    probs = [p[:6] for p in ok] + [(32, 32, lam_u, mu_u, gx, gy)]
+    results, report = P.batch_solve(probs, dtype="f32", tol=1e-7, check_every=100, max_iters=200_000)
+    assert results[0]["status"] == P.LBM_OK and results[1]["status"] == P.LBM_OK
+    assert results[2]["status"] == P.LBM_ERR_DIVERGED
+    # a cap below the steps needed gives NOT_CONVERGED at the first check past it
+    results, _ = P.batch_solve([p[:6] for p in ok], dtype="f32", tol=1e-12, check_every=100,
+                               max_iters=250)
+    for r in results:
+        assert r["status"] == P.LBM_ERR_NOT_CONVERGED and r["iters"] == 300
+
+
+def test_batch_autotune_cache_is_used(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("LBM_AUTOTUNE_CACHE", str(cache))
+    probs = [p[:6] for p in make_problems([(64, 64), (100, 60), (30, 30)], seed=5)]
+    _, rep1 = P.batch_solve(probs, tol=1e-6, check_every=50)
+    text = cache.read_text()
+    assert text.strip().endswith(str(rep1["tile_v"]))
+    _, rep2 = P.batch_solve(probs, tol=1e-6, check_every=50)
+    assert rep2["tile_v"] == rep1["tile_v"]
+
+
+def test_batch_rejects_bad_arguments():
+    probs = [p[:6] for p in make_problems([(8, 8)])]
+    with pytest.raises(P.LBMError):
+        P.batch_solve(probs, dtype="f64")
+    with pytest.raises(P.LBMError):
+        P.batch_solve(probs, check_every=1)
