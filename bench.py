@@ -291,6 +291,10 @@ def run_ours(args, ws, rank, local):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, gx, gy, torch, P, ws, dist if ws > 1 else None)
+    del gx_d, gy_d
+    torch.cuda.empty_cache()
+    batched = None if (args.no_batched or args.quick) else run_batched(args, P)
+    served = None if (args.no_served or args.quick) else run_served(args, P)
 
     if rank == 0:
         line = {
@@ -311,6 +315,8 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": res["launches"],
             "e2e": e2e,
             "variants": variants,
+            "batched": batched,
+            "served": served,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
@@ -360,6 +366,114 @@ def run_e2e(args, gx, gy, torch, P, ws, dist):
                    "lbm_get_displacement/lbm_get_stress(host)"}
 
 
+# ---------------------------------------------------------------------------
+# Batched and served workloads (time-boxed seeded subsets)
+# ---------------------------------------------------------------------------
+
+def plain_solve(P, p, tol, k, dtype="f32"):
+    """One problem through the plain single-lattice API, host in and out."""
+    gx, gy = W.random_force_grid(p.force)
+    with P.Lattice(p.nx, p.ny, p.lam, p.mu, dtype) as lat:
+        lat.set_force(gx, gy)
+        st, it, r = lat.solve(tol, 10_000_000, k)
+        lat.fields()
+    return st, it
+
+
+def run_batched(args, P):
+    """Config-4 stream (2048 problems, sides log-uniform in [32, 1024], nu in
+    [0, 0.45], 8 random force modes, FP32, tol 1e-8): the problems whose longer
+    side is at most --batched-cap, solved once in one arena and once one at a
+    time through lbm_solve.  Both through the public API, host in and out."""
+    probs = [p for p in W.batched_problems() if max(p.nx, p.ny) <= args.batched_cap]
+    probs = probs[:args.batched_max]
+    plist = []
+    for p in probs:
+        gx, gy = W.random_force_grid(p.force)
+        plist.append((p.nx, p.ny, p.lam, p.mu, gx, gy))
+    P.batch_solve(plist[:8], "f32", args.tol, args.check_every)          # warm-up
+    t0 = time.perf_counter()
+    res, rep = P.batch_solve(plist, "f32", args.tol, args.check_every)
+    tb = time.perf_counter() - t0
+    ok = sum(1 for r in res if r["status"] == 0)
+    t0 = time.perf_counter()
+    iters = 0
+    for p in probs:
+        st, it = plain_solve(P, p, args.tol, args.check_every)
+        iters += it
+    tp = time.perf_counter() - t0
+    return {"workload": "config-4 stream (seed %#x), the %d problems with max side <= %d, FP32, "
+                        "tol %g, residual every %d steps" % (0x5EED_BA7C4ED, len(probs),
+                                                             args.batched_cap, args.tol,
+                                                             args.check_every),
+            "problems": len(probs), "converged": ok,
+            "solves_per_s": len(probs) / tb, "plain_solves_per_s": len(probs) / tp,
+            "speedup_vs_plain": tp / tb, "wall_s": tb, "plain_wall_s": tp,
+            "lattice_updates": rep["lattice_updates"],
+            "glups_device": rep["lattice_updates"] / (rep["device_ms"] / 1e3) / 1e9,
+            "tile_v": rep["tile_v"], "chunks": rep["chunks"], "blocks": rep["blocks"]}
+
+
+def run_served(args, P):
+    """Config-5 stream (Poisson arrivals, sides log-uniform in [64, 4096], nu in
+    [0, 0.45], 8 random force modes, tol 1e-8, FP32 or FP16-shifted per request,
+    HBM budget 150 GB): the first --served-max requests with max side <= --served-cap,
+    arriving at --served-rate requests/s, through lbm_server_*; compared with a
+    single-server queue of plain lbm_solve calls on the same requests."""
+    import threading
+    stream = W.served_requests(rate_hz=args.served_rate)
+    picked = [i for i, r in enumerate(stream) if max(r.nx, r.ny) <= args.served_cap]
+    picked = picked[:args.served_max]
+    reqs = [stream[i] for i in picked]
+    # Thinning a Poisson stream by the side cap keeps it Poisson at rate
+    # rate * p; rescaling its clock by p restores the stated arrival rate.
+    p_keep = len(picked) / float(picked[-1] + 1)
+    t_first = reqs[0].arrival
+    for r in reqs:
+        r.arrival = t_first + (r.arrival - t_first) * p_keep
+    forces = [W.random_force_grid(r.force) for r in reqs]
+    tickets = [None] * len(reqs)
+    with P.Server(int(150e9), check_every=args.check_every) as srv:
+        start = time.perf_counter()
+
+        def feeder():
+            for i, r in enumerate(reqs):
+                delay = (r.arrival - t_first) - (time.perf_counter() - start)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[i] = srv.submit(r.nx, r.ny, r.lam, r.mu, forces[i][0], forces[i][1],
+                                        dtype=r.dtype, tol=args.tol)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        statuses = [srv.wait(t, 3600.0, fields=False)["status"] for t in tickets]
+        st = srv.stats()
+    # plain: each request alone through lbm_solve, served first-come first-served
+    service = []
+    for r in reqs:
+        t0 = time.perf_counter()
+        plain_solve(P, r, args.tol, args.check_every, r.dtype)
+        service.append(time.perf_counter() - t0)
+    done, lat = 0.0, []
+    for r, s in zip(reqs, service):
+        arr = r.arrival - t_first
+        done = max(done, arr) + s
+        lat.append((done - arr) * 1e3)
+    lat = np.array(lat)
+    return {"workload": "config-5 stream (seed %#x): first %d requests with max side <= %d, "
+                        "Poisson arrivals at %g req/s, tol %g, FP32/FP16S per request, "
+                        "150 GB budget" % (0x5E4FED, len(reqs), args.served_cap,
+                                           args.served_rate, args.tol),
+            "requests": len(reqs), "converged": statuses.count(0),
+            "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"],
+            "p99_ms": st["p99_ms"], "peak_running": st["peak_running"],
+            "plain_solves_per_s": len(reqs) / (done - 0.0) if done > 0 else None,
+            "plain_p50_ms": float(np.percentile(lat, 50)), "plain_p95_ms": float(np.percentile(lat, 95)),
+            "plain_p99_ms": float(np.percentile(lat, 99)),
+            "plain_service_s": float(sum(service))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,6 +493,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--ref-iters", type=int, default=40)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-cap", type=int, default=256)
+    ap.add_argument("--batched-max", type=int, default=2048)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-cap", type=int, default=256)
+    ap.add_argument("--served-max", type=int, default=300)
+    ap.add_argument("--served-rate", type=float, default=300.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

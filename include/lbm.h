@@ -150,7 +150,8 @@ int lbm_iterate_checked(lbm_ctx *ctx, int64_t n, int check_every, double *out);
  * ||d u/dt|| < TOL "in some norm").  Reading used: every check_every (= k)
  * steps, r = max_x |u^n - u^(n-k)|_inf / (k max_x |u^n|_inf), accumulated in
  * FP64 (r = 0 when u = 0).  The first check after a reset only takes the
- * snapshot.  Stops when r < tol (LBM_OK), when a non-finite displacement
+ * snapshot.  When tol is below the storage's rounding floor for k-step
+ * windows (see lbm_batch_solve), the window is stretched to a multiple of k.  Stops when r < tol (LBM_OK), when a non-finite displacement
  * appears (LBM_ERR_DIVERGED) or after max_iters steps
  * (LBM_ERR_NOT_CONVERGED).  iters_out / residual_out (nullable) receive the
  * steps taken in this call and the last r.  Synchronous. */
@@ -228,13 +229,80 @@ typedef struct lbm_batch_report {
 
 /* Solve `count` problems to residual tol (checked every check_every >= 2
  * steps; a problem stops at the first check below tol, at divergence, or at
- * the first check at or beyond max_iters steps).  dtype: LBM_F32 or LBM_F16S.
+ * the first check at or beyond max_iters steps).  Rounding keeps a stored
+ * state jittering by about J |u| (J ~ 2e-7 for FP32, 3e-5 for FP16-shifted,
+ * measured), which floors a w-step residual near J / w; a problem whose tol
+ * is below that for w = check_every is checked over windows of
+ * check_every * max(1, ceil(2 J / (tol * check_every))) steps instead.  dtype: LBM_F32 or LBM_F16S.
  * results[i] receives status, steps, residual and, where the pointers are
  * non-null, the FP64 displacement and stress (Table 2).  report may be null.
  * Synchronous.  Returns LBM_OK when every problem was run (per-problem
  * outcomes are in results), LBM_ERR_ARG / LBM_ERR_OOM / LBM_ERR_CUDA otherwise. */
 int lbm_batch_solve(int count, const lbm_problem *probs, int dtype, double tol, int check_every,
                     int64_t max_iters, lbm_result *results, lbm_batch_report *report);
+
+/* ---------------------------------------------------------------------------
+ * Continuous-batching solve server.  A worker thread owns two packed arenas
+ * (FP32 and FP16-shifted storage, half of the HBM budget each).  Submitted
+ * requests are copied and queued; between chunks of check_every steps the
+ * worker admits queued requests whose lattice fits the free arena memory
+ * (oldest first; a request bypassed for more than 50 chunks stops later
+ * admissions to its arena until it fits), runs one chunk of every resident
+ * problem (lbm_batch_solve's kernel and residual check), and retires problems
+ * that converged, diverged or hit max_iters: their fields are recovered into
+ * server-owned host memory and their arena memory is reused.  Requests that
+ * arrive while others run are therefore solved concurrently with them; a
+ * problem's arithmetic does not depend on what else is resident, so its result
+ * is the same alone and in the mix.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_server lbm_server;
+
+/* Returned by lbm_server_poll / lbm_server_wait while a request is not done. */
+#define LBM_PENDING 1
+
+typedef struct lbm_stats {
+    int64_t submitted, completed, queued, running;
+    double p50_ms, p95_ms, p99_ms, mean_ms;  /* submission -> completion latency */
+    double solves_per_s;       /* completed / (last completion - first submission) */
+    int64_t lattice_updates;   /* sum of nodes x steps of completed problems */
+    double device_ms;          /* device time of all chunks */
+    int64_t chunks;
+    size_t hbm_bytes;          /* device memory held by the arenas */
+    int peak_running;          /* most problems resident at once */
+    int tile_v;                /* tile width in warps of 32 columns */
+    int failed;                /* LBM_OK, or the error that stopped the worker */
+} lbm_stats;
+
+/* Start a server on the current device with an HBM budget (bytes, >= 1 MiB)
+ * for the two arenas; residual checked every check_every >= 2 steps. */
+int lbm_server_create(size_t hbm_budget_bytes, int check_every, lbm_server **out);
+
+/* Stop the worker (requests still running are abandoned) and free
+ * everything.  Null is ignored. */
+void lbm_server_destroy(lbm_server *srv);
+
+/* Queue one solve: problem (copied; its host arrays may be freed after the
+ * call), dtype LBM_F32 or LBM_F16S, tolerance, step cap.  *ticket identifies
+ * it.  LBM_ERR_ARG for a malformed request or a lattice that cannot fit the
+ * arena's half of the budget. */
+int lbm_server_submit(lbm_server *srv, const lbm_problem *prob, int dtype, double tol,
+                      int64_t max_iters, uint64_t *ticket);
+
+/* Non-blocking: LBM_PENDING while the request is queued or running;
+ * otherwise fills out (status, iters, residual, and the fields into its
+ * non-null host arrays of nx*ny doubles each), forgets the ticket and returns
+ * LBM_OK.  LBM_ERR_ARG for an unknown ticket. */
+int lbm_server_poll(lbm_server *srv, uint64_t ticket, lbm_result *out);
+
+/* Like lbm_server_poll but waits up to timeout_s seconds. */
+int lbm_server_wait(lbm_server *srv, uint64_t ticket, double timeout_s, lbm_result *out);
+
+/* Drop a request (queued: removed; running: released at the next chunk
+ * boundary; done: result discarded).  The ticket becomes unknown. */
+int lbm_server_cancel(lbm_server *srv, uint64_t ticket);
+
+/* Counters and latency percentiles of the requests completed so far. */
+int lbm_server_stats(lbm_server *srv, lbm_stats *out);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free residual-checked step.  The paper has no counterpart: this

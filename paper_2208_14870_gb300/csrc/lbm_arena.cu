@@ -83,10 +83,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_arena_chunk(const BatchArgs A) 
     __shared__ float red[kRes][kThreads / 32];
     const int ntiles = *A.ntiles;
     for (int s = 0; s < A.nsteps; ++s) {
-        const bool check = (s == A.nsteps - 1);
+        const bool last = (s == A.nsteps - 1);
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const uint2 tl = A.tiles[t];
             const BatchProb P = A.probs[tl.x];
+            const bool check = last && P.check;  // uniform over the block
             float acc[kRes] = {0.f, 0.f, 0.f, 0.f, 0.f};
             if (!check) {
                 arena_tile<S, V, false>(A, P, (int)tl.y, s, acc);

@@ -9,9 +9,10 @@
 // placed by a first-fit allocator (256-byte aligned).  The work of one step
 // is the list of (problem, tile) pairs of the active problems; the kernel
 // walks that list grid-stride, then synchronises the whole grid before the
-// next step (cooperative launch).  The last step of each chunk carries the
-// residual check; its per-problem partial sums go to per-problem FP64
-// accumulators with atomics.  The host reads them after the chunk, retires
+// next step (cooperative launch).  The last step of a chunk carries the
+// residual check for the problems flagged in their descriptor (a problem
+// checks every `check_period` chunks of its own steps); its per-problem
+// partial sums go to per-problem FP64 accumulators with atomics.  The host reads them after the chunk, retires
 // converged problems, admits new ones and rebuilds the tile list between
 // chunks; the chunk itself (accumulator reset, kernel, accumulator read-back)
 // is replayed from a CUDA graph.
@@ -31,7 +32,7 @@ struct BatchProb {
     int64_t pop_off;   // bytes into each population buffer
     int64_t car_off;   // bytes into each carrier buffer (F16S)
     int64_t fs_off;    // bytes into the force/snapshot buffer
-    int nx, ny, ntx, dtype, parity;
+    int nx, ny, check, dtype, parity;   // check: this chunk's last step checks
     float a11, as, ad, theta, hscale, hinv;
 };
 

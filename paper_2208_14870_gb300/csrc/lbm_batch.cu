@@ -3,6 +3,7 @@
 // width chosen by the autotuner.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -88,6 +89,10 @@ extern "C" int lbm_batch_solve(int count, const lbm_problem* probs, int dtype, d
         // 32, 64 and 128 and the fastest per tile-step is kept and cached.
         const std::string key = signature(count, probs, dtype, check_every);
         int V = rc == LBM_OK ? autotune_lookup(key) : 0;
+        if (const char* force_v = std::getenv("LBM_BATCH_TILE_V")) {  // fixed width, no tuning
+            const int fv = std::atoi(force_v);
+            if (fv == 1 || fv == 2 || fv == 4) V = fv;
+        }
         const int cand[3] = {1, 2, 4};
         double best = 1e300;
         int tuning = V == 0 ? 0 : 3;

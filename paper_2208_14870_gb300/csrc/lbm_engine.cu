@@ -180,6 +180,7 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
     p.hexp = dtype_ == S_F16S ? f16s_exponent(gmax, nx, ny) : 0;
     p.tol = tol;
     p.max_iters = max_iters;
+    p.period = check_period(dtype_, tol, k_);
     p.state = P_RUNNING;
     probs_[slot] = p;
     ++nrunning_;
@@ -300,6 +301,14 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
         int rc = upload_tiles(V, err);
         if (rc) return rc;
     }
+    for (auto& p : probs_) {
+        if (p.state != P_RUNNING) continue;
+        const bool now = ((p.steps + k_) % ((int64_t)k_ * p.period)) == 0;
+        if (now != p.check_now) {
+            p.check_now = now;
+            desc_dirty_ = true;
+        }
+    }
     if (desc_dirty_) {
         std::vector<BatchProb> d(probs_.size());
         for (size_t i = 0; i < probs_.size(); ++i) {
@@ -310,7 +319,7 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
             b.fs_off = p.fs_off;
             b.nx = p.nx;
             b.ny = p.ny;
-            b.ntx = 0;
+            b.check = p.check_now ? 1 : 0;
             b.dtype = dtype_;
             b.parity = p.parity;
             b.a11 = p.a11;
@@ -359,7 +368,9 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
         }
         const double* raw = h_acc_ + (int64_t)s * kRes;
         bool done = false;
-        if (raw[4] != 0.0 || !std::isfinite(raw[0]) || !std::isfinite(raw[1])) {
+        if (!p.check_now) {
+            // no residual this chunk
+        } else if (raw[4] != 0.0 || !std::isfinite(raw[0]) || !std::isfinite(raw[1])) {
             p.status = LBM_ERR_DIVERGED;
             p.residual = INFINITY;
             done = true;
@@ -367,7 +378,8 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
             p.snap_valid = true;
             p.residual = INFINITY;
         } else {
-            p.residual = raw[1] > 0.0 ? raw[0] / ((double)k_ * raw[1]) : 0.0;
+            const double window = (double)k_ * p.period;
+            p.residual = raw[1] > 0.0 ? raw[0] / (window * raw[1]) : 0.0;
             if (p.residual < p.tol) {
                 p.status = LBM_OK;
                 done = true;

@@ -29,6 +29,8 @@ struct HostProb {
     int64_t max_iters = 0;
     double tol = 0.0;
     bool snap_valid = false;
+    bool check_now = false;    // the coming chunk checks this problem
+    int period = 1;            // residual window = period chunks
     int status = 0;            // lbm status when done
     double residual = 0.0;
     int64_t lups = 0;          // nodes x steps

@@ -95,6 +95,30 @@ __device__ __forceinline__ void gather(const StepParams& a, int64_t r0, int64_t 
     }
 }
 
+// FP16-shifted store of one node: the deviations N (unscaled, FP32) are
+// rounded to FP16, and the FP32 carriers absorb the first moments of the
+// ROUNDED deviations, c10 = m*_10 - m_10(N_rounded), so that the stored state
+// N_rounded + E(c) keeps the first moments m*_10, m*_01 exactly (E(c) has
+// first moments c, no second moments).  Without this, the rounding of N would
+// feed the conserved mean-displacement mode every step and u would drift.
+__device__ __forceinline__ void store_f16s(const StepParams& a, int64_t idx, const float n[8],
+                                           float m10s, float m01s) {
+    __half* d = static_cast<__half*>(a.dst);
+    const int64_t pl = a.plane;
+    const float hs = a.hscale, hi = a.hinv;
+    float r[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const __half h = __float2half_rn(n[p] * hs);
+        d[p * pl + idx] = h;
+        r[p] = __half2float(h) * hi;
+    }
+    const float e10 = (r[0] - r[2]) + ((r[4] - r[6]) - (r[5] - r[7]));
+    const float e01 = (r[1] - r[3]) + ((r[4] - r[6]) + (r[5] - r[7]));
+    a.cdst[idx] = m10s - e10;
+    a.cdst[pl + idx] = m01s - e01;
+}
+
 // Store the post-collision state of node idx.
 template <int S>
 __device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
@@ -107,11 +131,7 @@ __device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
     T f[8];
     if constexpr (S == S_F16S) {
         populations(deviation_moments(s, theta), f);
-        const float hs = a.hscale;
-#pragma unroll
-        for (int p = 0; p < 8; ++p) d[p * pl + idx] = __float2half_rn(f[p] * hs);
-        a.cdst[idx] = s.m10;
-        a.cdst[pl + idx] = s.m01;
+        store_f16s(a, idx, f, s.m10, s.m01);
     } else {
         (void)theta;
         populations(s, f);
@@ -363,9 +383,8 @@ k_import(const StepParams a, typename StoreT<S>::T theta, const double* in) {
         const Mom<T> s = moments(fs);
         T nf[8];
         populations(deviation_moments(s, theta), nf);
-        for (int p = 0; p < 8; ++p) d[p * a.plane + idx] = __float2half_rn(nf[p] * a.hscale);
-        a.cdst[idx] = s.m10;
-        a.cdst[a.plane + idx] = s.m01;
+        (void)d;
+        store_f16s(a, idx, nf, s.m10, s.m01);
     } else {
         (void)theta;
         for (int p = 0; p < 8; ++p) d[p * a.plane + idx] = P(fs[p]);
@@ -415,6 +434,20 @@ inline int f16s_exponent(double gmax, int nx, int ny) {
     const double L = double(nx > ny ? nx : ny);
     int e = 8 - (int)ceil(log2(gmax * L));
     return e < -60 ? -60 : (e > 60 ? 60 : e);
+}
+
+// Residual windows per check interval k: rounding keeps a stored state
+// jittering by about J |u| (J ~ 3e-15 for FP64, 2e-7 for FP32, 3e-5 for
+// FP16-shifted storage, measured), which floors a w-step residual near J / w;
+// a problem asking for tol is therefore checked every
+// min(64, max(1, ceil(2 J / (tol k)))) intervals of k steps.  The cap keeps
+// divergence detection (made at checks) within 64 intervals; a tol that would
+// need more is below what the storage type can resolve.
+inline int check_period(int dtype, double tol, int k) {
+    const double J = dtype == S_F16S ? 3e-5 : (dtype == S_F32 ? 2e-7 : 3e-15);
+    if (!(tol > 0.0) || k < 1) return 64;
+    const double p = ceil(2.0 * J / (tol * (double)k));
+    return p < 1.0 ? 1 : (p > 64.0 ? 64 : (int)p);
 }
 
 inline int64_t step_tiles(int nx, int ny, int V) {

@@ -411,3 +411,109 @@ def batch_solve(problems, dtype: str = "f32", tol: float = 1e-8, check_every: in
         results.append(d)
     report = {k: getattr(rep, k) for k, _ in lbm_batch_report._fields_}
     return results, report
+
+
+# ---------------------------------------------------------------------------
+# Continuous-batching server (lbm_server_*)
+# ---------------------------------------------------------------------------
+
+LBM_PENDING = 1
+
+
+class lbm_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p95_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("lattice_updates", ctypes.c_int64),
+                ("device_ms", ctypes.c_double), ("chunks", ctypes.c_int64),
+                ("hbm_bytes", ctypes.c_size_t), ("peak_running", ctypes.c_int),
+                ("tile_v", ctypes.c_int), ("failed", ctypes.c_int)]
+
+
+for _name, _res, _args in (
+        ("lbm_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)]),
+        ("lbm_server_destroy", None, [_vp]),
+        ("lbm_server_submit", ctypes.c_int, [_vp, ctypes.POINTER(lbm_problem), ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_int64,
+                                             ctypes.POINTER(ctypes.c_uint64)]),
+        ("lbm_server_poll", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(lbm_result)]),
+        ("lbm_server_wait", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double,
+                                           ctypes.POINTER(lbm_result)]),
+        ("lbm_server_cancel", ctypes.c_int, [_vp, ctypes.c_uint64]),
+        ("lbm_server_stats", ctypes.c_int, [_vp, ctypes.POINTER(lbm_stats)])):
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class Server:
+    """Continuous-batching solve server on the current CUDA device."""
+
+    def __init__(self, hbm_budget_bytes: int, check_every: int = 100):
+        out = _vp()
+        _check(_lib.lbm_server_create(int(hbm_budget_bytes), int(check_every), ctypes.byref(out)),
+               "lbm_server_create")
+        self.srv = out.value
+        self._shapes = {}
+
+    def close(self):
+        if getattr(self, "srv", None):
+            _lib.lbm_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, nx, ny, lam, mu, gx, gy, dtype="f32", tol=1e-8, max_iters=10_000_000) -> int:
+        gxh = _host_f64(gx, nx * ny)
+        gyh = _host_f64(gy, nx * ny)
+        prob = lbm_problem(nx, ny, lam, mu, gxh.ctypes.data, gyh.ctypes.data)
+        t = ctypes.c_uint64()
+        _check(_lib.lbm_server_submit(self.srv, ctypes.byref(prob), DTYPES[dtype], tol, max_iters,
+                                      ctypes.byref(t)), "lbm_server_submit")
+        self._shapes[t.value] = (nx, ny)
+        return t.value
+
+    def _result(self, fn, ticket, *extra, fields=True):
+        if ticket not in self._shapes:  # let the library reject it
+            _check(fn(self.srv, ticket, *extra, None), fn.__name__)
+        nx, ny = self._shapes[ticket]
+        res = lbm_result()
+        out = None
+        if fields:
+            out = np.empty((5, ny, nx), dtype=np.float64)
+            res.ux, res.uy, res.sxx, res.syy, res.sxy = [out[c].ctypes.data for c in range(5)]
+        st = fn(self.srv, ticket, *extra, ctypes.byref(res))
+        if st == LBM_PENDING:
+            return None
+        _check(st, fn.__name__)
+        del self._shapes[ticket]
+        d = {"status": res.status, "iters": res.iters, "residual": res.residual}
+        if fields:
+            d["fields"] = out
+        return d
+
+    def poll(self, ticket: int, fields: bool = True):
+        return self._result(_lib.lbm_server_poll, ticket, fields=fields)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0, fields: bool = True):
+        return self._result(_lib.lbm_server_wait, ticket, ctypes.c_double(timeout_s), fields=fields)
+
+    def cancel(self, ticket: int):
+        _check(_lib.lbm_server_cancel(self.srv, ticket), "lbm_server_cancel")
+        self._shapes.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = lbm_stats()
+        _check(_lib.lbm_server_stats(self.srv, ctypes.byref(s)), "lbm_server_stats")
+        return {k: getattr(s, k) for k, _ in lbm_stats._fields_}

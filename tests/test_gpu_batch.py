@@ -24,8 +24,12 @@ def _tune_cache(tmp_path, monkeypatch):
 
 
 def rel_per_field(a, b):
-    return max(float(np.max(np.abs(a[i] - b[i]))) / max(float(np.max(np.abs(b[i]))), 1e-300)
-               for i in range(a.shape[0]))
+    """Displacement error relative to max |u| over both components, stress
+    error relative to the largest stress component (a field that is tiny for a
+    given force is not measured against its own maximum)."""
+    eu = float(np.max(np.abs(a[:2] - b[:2]))) / max(float(np.max(np.abs(b[:2]))), 1e-300)
+    es = float(np.max(np.abs(a[2:] - b[2:]))) / max(float(np.max(np.abs(b[2:]))), 1e-300)
+    return max(eu, es)
 
 
 SIZES = [(33, 17), (64, 64), (130, 7), (40, 96), (1, 9), (200, 150), (77, 77), (16, 300),
@@ -44,11 +48,14 @@ def make_problems(sizes, seed=0):
     return probs
 
 
-@pytest.mark.parametrize("dtype,tol_fix", [("f32", 2e-5), ("f16s", 2e-3)])
-def test_batch_matches_single_lattice_and_fixed_point(dtype, tol_fix):
+# Residual tolerance and window per storage: the stopping error is about
+# r / (slowest decay rate), ~3.7e-4 per step for the 200-node side here, so
+# FP32 stops at 2e-9 (window 200 keeps its rounding floor below) and FP16S at
+# 2e-7 with a window of 1000 steps (its rounding floor is near 4e-5 / k).
+@pytest.mark.parametrize("dtype,tol,k,tol_fix", [("f32", 2e-9, 200, 2e-5), ("f16s", 2e-7, 1000, 2e-3)])
+def test_batch_matches_single_lattice_and_fixed_point(dtype, tol, k, tol_fix):
     probs = make_problems(SIZES)
-    k = 50
-    results, report = P.batch_solve([p[:6] for p in probs], dtype=dtype, tol=1e-7 if dtype == "f32" else 1e-6,
+    results, report = P.batch_solve([p[:6] for p in probs], dtype=dtype, tol=tol,
                                     check_every=k, max_iters=2_000_000)
     assert report["tile_v"] in (1, 2, 4) and report["chunks"] >= 3
     for (nx, ny, lam, mu, gx, gy, pw), r in zip(probs, results):
@@ -62,7 +69,7 @@ def test_batch_matches_single_lattice_and_fixed_point(dtype, tol_fix):
         # the single-lattice path with the same checks stops at the same step
         with P.Lattice(nx, ny, lam, mu, dtype) as lat:
             lat.set_force(gx, gy)
-            st, iters, res = lat.solve(1e-7 if dtype == "f32" else 1e-6, 2_000_000, k)
+            st, iters, res = lat.solve(tol, 2_000_000, k)
             assert st == P.LBM_OK
             assert abs(iters - r["iters"]) <= k
             # same arithmetic, but the compiler may contract a*b+c into FMAs
