@@ -44,7 +44,13 @@ BYTES_PER_LUP = {"f64": 8 * 8 * 2 + 2 * 8, "f32": 8 * 4 * 2 + 2 * 4, "f16s": (8 
 FORCE_SEED = 0x2208_14870
 # DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype,
 # with the hash of the kernel sources it was taken on (null once they change).
-NCU_TRAFFIC = {}
+# Captured on 4096^2 (profiles/k_step_*_4096_full.md) and scaled by the node
+# count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
+# small launch are not counted, so these slightly undercount.
+NCU_TRAFFIC = {
+    "f32": {"bytes_per_launch": (671.151104e6 + 486.694144e6) * 16, "kernel_hash": "6afdc4f569210cf7"},
+    "f16s": {"bytes_per_launch": (536.964608e6 + 366.787840e6) * 16, "kernel_hash": "6afdc4f569210cf7"},
+}
 
 
 def kernel_hash() -> str:
@@ -501,10 +507,19 @@ def main():
     ap.add_argument("--served-cap", type=int, default=256)
     ap.add_argument("--served-max", type=int, default=300)
     ap.add_argument("--served-rate", type=float, default=300.0)
+    ap.add_argument("--only", choices=["batched", "served"], default=None,
+                    help="run one secondary workload alone and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     ws, rank, local = dist_setup()
+    if args.only:
+        import torch
+        torch.cuda.set_device(local)
+        import paper_2208_14870_gb300 as P
+        out = run_batched(args, P) if args.only == "batched" else run_served(args, P)
+        print(json.dumps({"only": args.only, **out}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
     else:
