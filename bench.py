@@ -48,16 +48,27 @@ FORCE_SEED = 0x2208_14870
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32": {"bytes_per_launch": (671.151104e6 + 486.694144e6) * 16, "kernel_hash": "6afdc4f569210cf7"},
-    "f16s": {"bytes_per_launch": (536.964608e6 + 366.787840e6) * 16, "kernel_hash": "6afdc4f569210cf7"},
+    "f32": {"bytes_per_launch": (671.151104e6 + 486.694144e6) * 16, "kernel_hash": "edb850198410e1fd"},
+    "f16s": {"bytes_per_launch": (536.964608e6 + 366.787840e6) * 16, "kernel_hash": "edb850198410e1fd"},
 }
 
 
+def kernel_source(text: str) -> str:
+    """The part of lbm_kernels.cuh that defines the stream-collide kernel
+    (gather, stores, residual reduction, tile body, k_step)."""
+    a = text.index("// Gather the pre-collision populations")
+    b = text.index("// Solution fields of the current state")
+    return text[a:b]
+
+
 def kernel_hash() -> str:
+    """Hash of the stream-collide kernel's source: per-node arithmetic
+    (lbm_core.cuh), the kernel section of lbm_kernels.cuh and its launcher."""
+    d = os.path.join(ROOT, "paper_2208_14870_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("lbm_core.cuh", "lbm_kernels.cuh", "lbm_ops.cuh"):
-        with open(os.path.join(ROOT, "paper_2208_14870_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    h.update(open(os.path.join(d, "lbm_core.cuh"), "rb").read())
+    h.update(kernel_source(open(os.path.join(d, "lbm_kernels.cuh")).read()).encode())
+    h.update(open(os.path.join(d, "lbm_ops.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 

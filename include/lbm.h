@@ -128,6 +128,26 @@ int lbm_set_force(lbm_ctx *ctx, const double *gx, const double *gy);
  * maximum sets the storage scale). */
 int lbm_set_force_device(lbm_ctx *ctx, const double *gx, const double *gy);
 
+/* Body force with the higher-order correction of Sec. 4 (Eqs.
+ * force_correction_x/y, "improved scheme" of Sec. 6.3.2) applied on the device
+ * in lattice units with periodic central differences:
+ *   gx' = gx - (D1 dxx gx + D2 dxy gy + D3 dyy gx),
+ *   gy' = gy - (D3 dxx gy + D2 dxy gx + D1 dyy gy),
+ * dxx g = g(x+1) - 2g(x) + g(x-1), dxy g = (g(x+1,y+1) - g(x+1,y-1) - g(x-1,y+1)
+ * + g(x-1,y-1))/4.  d = {D1, D2, D3} (host, finite).  gx, gy as in
+ * lbm_set_force.  Synchronous.  The caller chooses D: the constants printed in
+ * Appendix B (lbm_error_constants) do not cancel the force-driven leading
+ * error of this scheme as printed (see the design notes), so they are an
+ * input here rather than computed. */
+int lbm_set_force_corrected(lbm_ctx *ctx, const double *gx, const double *gy, const double *d);
+
+/* The leading-order error constants as printed in Appendix B:
+ * out[0..4] = C1..C5, out[5..7] = D1..D3, for dimensionless Young's modulus E
+ * (> 0), Poisson's ratio nu (-1 < nu < 1), theta (0 = 1/3) and relaxation
+ * times tau12 = tau21 (0 = 1/2) and tau22 (0 = 1/2).  Host-only arithmetic. */
+int lbm_error_constants(double E, double nu, double theta, double tau12, double tau22,
+                        double *out);
+
 /* Back to the zero state (Eq. init_cond with u_0 = 0); step counter 0; the
  * residual snapshot is invalidated.  The force is kept.  Enqueued only. */
 int lbm_reset(lbm_ctx *ctx);

@@ -411,6 +411,72 @@ int lbm_set_force(lbm_ctx* c, const double* gx, const double* gy) {
     return LBM_OK;
 }
 
+int lbm_set_force_corrected(lbm_ctx* c, const double* gx, const double* gy, const double* d) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!gx || !gy || !d) return fail(LBM_ERR_ARG, "lbm_set_force_corrected: null pointer");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(d[i])) return fail(LBM_ERR_ARG, "lbm_set_force_corrected: non-finite D");
+    rc = ensure_staging(c, 4 * c->n);
+    if (rc) return rc;
+    double* in = c->staging;
+    double* out = c->staging + 2 * c->n;
+    CK(cudaMemcpyAsync(in, gx, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(in + c->n, gy, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    k_force_correct<<<1024, 256, 0, c->stream>>>(in, in + c->n, out, out + c->n, c->nx, c->ny, d[0],
+                                                 d[1], d[2]);
+    CK(cudaGetLastError());
+    rc = set_force_dev(c, out, out + c->n);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_error_constants(double E, double nu, double theta, double tau12, double tau22, double* out) {
+    if (!out) return fail(LBM_ERR_ARG, "lbm_error_constants: null output");
+    if (theta == 0.0) theta = 1.0 / 3.0;
+    if (tau12 == 0.0) tau12 = 0.5;
+    if (tau22 == 0.0) tau22 = 0.5;
+    if (!(E > 0.0) || !(nu > -1.0 && nu < 1.0) || !(theta > 0.0 && theta < 1.0))
+        return fail(LBM_ERR_ARG, "lbm_error_constants: need E > 0, -1 < nu < 1, 0 < theta < 1");
+    // Appendix B as printed (tau_21 = tau_12).
+    const double th = theta, t12 = tau12, t21 = tau12, t22 = tau22;
+    const double c = 1.0 - th * th, d = 1.0 - nu * nu, E2 = E * E, E3 = E2 * E;
+    const double q = th * th * (1.0 + nu) + nu - 2.0 * th - 1.0;
+    out[0] = (nu * nu - 2.0 * th * nu + 1.0) / (c * d * d * d) * E3 +
+             th * (nu - th) * t12 / (c * d * d) * E2 +
+             (-1.0 + th * th + 12.0 * th * (th - nu) * t12 * t22) / (12.0 * c * d) * E;
+    out[1] = ((1.0 - nu) * (1.0 - nu) * (1.0 - nu) + 4.0 * th * (nu * nu * nu - nu * nu + 3.0 * nu + 1.0) +
+              th * th * (5.0 * nu * nu * nu - 15.0 * nu * nu - nu - 5.0)) / (8.0 * c * d * d * d) * E3 +
+             (2.0 * th * ((1.0 - nu) * nu + th * th * (1.0 + nu) - th * (1.0 + nu * nu)) * t12 +
+              (1.0 - th) * (1.0 - nu) * (1.0 + 2.0 * th - nu - th * th * (1.0 + nu)) * t21) /
+                 (-4.0 * th * c * d * d) * E2 +
+             ((2.0 * th * th - 3.0 * th + 1.0) * (1.0 + 3.0 * th * (1.0 - nu) - 5.0 * nu) +
+              24.0 * th * (th - nu) * t12 * t22) / (24.0 * c * d) * E;
+    out[2] = ((1.0 - nu) * (1.0 - nu) * (3.0 + nu) + 4.0 * th * (-nu * nu * nu + 3.0 * nu * nu + nu + 1.0) -
+              th * th * (5.0 * nu * nu * nu - 3.0 * nu * nu + 7.0 * nu + 7.0)) / (8.0 * th * c * d * d * d) * E3 +
+             (-2.0 * (1.0 - th) * th * (nu - 2.0 * th - 1.0) * (1.0 - nu) * t12 -
+              ((1.0 + th) * (1.0 - nu) * (1.0 - nu) + th * th * th * (1.0 + nu) * (1.0 + nu) +
+               th * th * (nu * nu - 2.0 * nu - 3.0)) * t21) / (4.0 * th * c * d * d) * E2 +
+             ((1.0 - th) * (1.0 - nu - th * (1.0 + nu) - 2.0 * th * th * (2.0 + nu)) -
+              4.0 * c * (1.0 - nu) * t12 * t22 + 4.0 * q * t21 * t22) / (8.0 * c * d) * E +
+             th * t22 / 4.0;
+    out[3] = (16.0 * th * nu + (1.0 - nu) * (1.0 - nu) * (3.0 + nu) -
+              th * th * (nu * nu * nu + 9.0 * nu * nu - 5.0 * nu + 11.0)) / (8.0 * th * c * d * d * d) * E3 +
+             (c * (1.0 - nu) * (th * nu + nu + th - 1.0) * t12 - 2.0 * th * q * t21) / (4.0 * th * c * d * d) * E2 +
+             (c * (2.0 * (2.0 - nu) - 3.0 * th * (5.0 + nu)) - 12.0 * c * (1.0 - nu) * t12 * t22 +
+              12.0 * q * t21 * t22) / (24.0 * c * d) * E +
+             th * t22 / 4.0;
+    out[4] = E3 / (8.0 * th * (1.0 + nu) * (1.0 + nu) * (1.0 + nu)) -
+             (1.0 - th) * t12 / (4.0 * th * (1.0 + nu) * (1.0 + nu)) * E2 - (3.0 * th - 2.0) / (24.0 * (1.0 + nu)) * E;
+    out[5] = (nu * nu - 2.0 * th * nu + 1.0) / (c * d * d) * E2 + th * (nu - th) * t12 / (c * d * d) * E - 0.25;
+    out[6] = ((1.0 - nu) * (1.0 - nu) + 8.0 * th * nu - th * th * (5.0 * nu * nu - 2.0 * nu + 5.0)) /
+                 (4.0 * th * c * d * d) * E2 -
+             q * t21 / (2.0 * c * d * d) * E - th / 2.0;
+    out[7] = E2 / (4.0 * th * (1.0 + nu) * (1.0 + nu)) + t12 / (2.0 * (1.0 + nu)) * E - th / 4.0;
+    return LBM_OK;
+}
+
 int lbm_set_force_device(lbm_ctx* c, const double* gx, const double* gy) {
     int rc = check_ctx(c);
     if (rc) return rc;

@@ -410,6 +410,10 @@ __global__ void k_absmax(const double* gx, const double* gy, int64_t n,
 // F16S: multiply every stored deviation by `factor` (a power of two).
 __global__ void k_rescale_half(__half* h, int64_t count, float factor);
 
+// Higher-order force correction with periodic central differences (FP64).
+__global__ void k_force_correct(const double* gx, const double* gy, double* ox, double* oy, int nx,
+                                int ny, double d1, double d2, double d3);
+
 // Launchers (defined per storage type).
 template <int S>
 struct Ops {

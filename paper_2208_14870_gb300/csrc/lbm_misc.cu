@@ -31,3 +31,34 @@ __global__ void k_rescale_half(__half* h, int64_t count, float factor) {
 }
 
 }  // namespace lbm
+
+namespace lbm {
+
+// Higher-order force correction (Sec. 4, Eqs. force_correction_x/y) in
+// lattice units:
+//   gx' = gx - (D1 dxx gx + D2 dxy gy + D3 dyy gx)
+//   gy' = gy - (D3 dxx gy + D2 dxy gx + D1 dyy gy)
+// with periodic central differences per node spacing,
+//   dxx g = g(x+1) - 2 g(x) + g(x-1),  dxy g = (g(+,+) - g(+,-) - g(-,+) + g(-,-)) / 4.
+__global__ void k_force_correct(const double* gx, const double* gy, double* ox, double* oy, int nx,
+                                int ny, double d1, double d2, double d3) {
+    const int64_t n = (int64_t)nx * ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i - (int64_t)y * nx);
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x + 1 == nx ? 0 : x + 1;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
+        const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+        const double gxc = gx[r0 + x], gyc = gy[r0 + x];
+        const double gx_xx = gx[r0 + xp] - 2.0 * gxc + gx[r0 + xm];
+        const double gx_yy = gx[rp + x] - 2.0 * gxc + gx[rm + x];
+        const double gy_xx = gy[r0 + xp] - 2.0 * gyc + gy[r0 + xm];
+        const double gy_yy = gy[rp + x] - 2.0 * gyc + gy[rm + x];
+        const double gx_xy = 0.25 * (gx[rp + xp] - gx[rm + xp] - gx[rp + xm] + gx[rm + xm]);
+        const double gy_xy = 0.25 * (gy[rp + xp] - gy[rm + xp] - gy[rp + xm] + gy[rm + xm]);
+        ox[r0 + x] = gxc - (d1 * gx_xx + d2 * gy_xy + d3 * gx_yy);
+        oy[r0 + x] = gyc - (d3 * gy_xx + d2 * gx_xy + d1 * gy_yy);
+    }
+}
+
+}  // namespace lbm

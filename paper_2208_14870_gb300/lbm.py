@@ -59,6 +59,9 @@ _SIGS = {
     "lbm_set_stream": (_c.c_int, [_vp, _vp]),
     "lbm_set_force": (_c.c_int, [_vp, _vp, _vp]),
     "lbm_set_force_device": (_c.c_int, [_vp, _vp, _vp]),
+    "lbm_set_force_corrected": (_c.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_error_constants": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double, _c.c_double,
+                                       _c.c_double, _vp]),
     "lbm_reset": (_c.c_int, [_vp]),
     "lbm_iterate": (_c.c_int, [_vp, _i64]),
     "lbm_iterate_checked": (_c.c_int, [_vp, _i64, _c.c_int, _vp]),
@@ -145,6 +148,19 @@ def lbm_set_force(ctx: int, gx_ptr: int, gy_ptr: int) -> None:
 
 def lbm_set_force_device(ctx: int, gx_ptr: int, gy_ptr: int) -> None:
     _check(_lib.lbm_set_force_device(ctx, gx_ptr, gy_ptr), "lbm_set_force_device")
+
+
+def lbm_set_force_corrected(ctx: int, gx_ptr: int, gy_ptr: int, d_ptr: int) -> None:
+    _check(_lib.lbm_set_force_corrected(ctx, gx_ptr, gy_ptr, d_ptr), "lbm_set_force_corrected")
+
+
+def lbm_error_constants(E: float, nu: float, theta: float = 0.0, tau12: float = 0.0,
+                        tau22: float = 0.0) -> np.ndarray:
+    """[C1..C5, D1..D3] as printed in Appendix B."""
+    out = np.zeros(8)
+    _check(_lib.lbm_error_constants(E, nu, theta, tau12, tau22, out.ctypes.data),
+           "lbm_error_constants")
+    return out
 
 
 def lbm_reset(ctx: int) -> None:
@@ -282,6 +298,13 @@ class Lattice:
             return
         gxh, gyh = _host_f64(gx, self.n), _host_f64(gy, self.n)
         lbm_set_force(self.ctx, gxh.ctypes.data, gyh.ctypes.data)
+
+    def set_force_corrected(self, gx, gy, d):
+        """Host force with the higher-order correction (D1, D2, D3) applied on the device."""
+        gxh, gyh = _host_f64(gx, self.n), _host_f64(gy, self.n)
+        dd = np.ascontiguousarray(d, dtype=np.float64)
+        assert dd.shape == (3,)
+        lbm_set_force_corrected(self.ctx, gxh.ctypes.data, gyh.ctypes.data, dd.ctypes.data)
 
     def reset(self):
         lbm_reset(self.ctx)

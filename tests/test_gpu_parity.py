@@ -326,3 +326,23 @@ def test_mean_displacement_is_conserved(dtype, tol):
         u = lat.displacement()
     scale = float(np.max(np.abs(u)))
     assert abs(float(u[0].mean())) < tol * scale and abs(float(u[1].mean())) < tol * scale
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-10), ("f32", 2e-5)])
+def test_force_correction_matches_oracle(dtype, tol):
+    """lbm_set_force_corrected applies the higher-order force correction on
+    the device; the steady state equals the exact fixed point of the oracle's
+    corrected force (same central differences)."""
+    lam, mu = W.lame_2d(0.3, 0.25)
+    rates = oracle.relaxation_rates(lam, mu)
+    nx, ny = 48, 40
+    pw = W.random_force(nx, ny, 4, 3, seed=31)
+    gx, gy = W.random_force_grid(pw)
+    D = np.array([0.152, -0.016, -0.0199])
+    gxc, gyc = oracle.corrected_force_fd(gx, gy, D)
+    exact = oracle.fields(F.steady_state_grid(gxc, gyc, rates), gxc, gyc, rates)
+    with Lattice(nx, ny, lam, mu, dtype) as lat:
+        lat.set_force_corrected(gx, gy, D)
+        st, iters, r = lat.solve(1e-14 if dtype == "f64" else 2e-9, 10_000_000, 200)
+        assert st == P.LBM_OK
+        assert rel(lat.fields()[:2], exact[:2]) < tol
