@@ -148,6 +148,17 @@ int lbm_set_force_corrected(lbm_ctx *ctx, const double *gx, const double *gy, co
 int lbm_error_constants(double E, double nu, double theta, double tau12, double tau22,
                         double *out);
 
+/* Von Neumann stability (Sec. 4): sup over sampled wave vectors
+ * k = khat (cos phi, sin phi), khat in [0, pi] (nk >= 2 points), phi in
+ * [0, pi/4] (nphi >= 1 points), of the spectral radius of the one-step
+ * amplification matrix L(k) = diag(exp(-i k.c)) A, A of Eq. lbmvector with
+ * the Table 1 equilibria.  theta, tau12 (= tau21), tau22 as in lbm_options
+ * (0 = standard).  The scheme is stable when *rho <= 1 (the conserved
+ * k = 0 modes give exactly 1); the paper samples nk = 50, nphi = 5.
+ * Host-only; LBM_ERR_ARG for invalid parameters. */
+int lbm_spectral_radius(double lambda, double mu, double theta, double tau12, double tau22,
+                        int nk, int nphi, double *rho);
+
 /* Back to the zero state (Eq. init_cond with u_0 = 0); step counter 0; the
  * residual snapshot is invalidated.  The force is kept.  Enqueued only. */
 int lbm_reset(lbm_ctx *ctx);

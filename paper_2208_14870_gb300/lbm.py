@@ -60,6 +60,8 @@ _SIGS = {
     "lbm_set_force": (_c.c_int, [_vp, _vp, _vp]),
     "lbm_set_force_device": (_c.c_int, [_vp, _vp, _vp]),
     "lbm_set_force_corrected": (_c.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_spectral_radius": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double, _c.c_double,
+                                       _c.c_double, _c.c_int, _c.c_int, _c.POINTER(_c.c_double)]),
     "lbm_error_constants": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double, _c.c_double,
                                        _c.c_double, _vp]),
     "lbm_reset": (_c.c_int, [_vp]),
@@ -163,6 +165,16 @@ def lbm_error_constants(E: float, nu: float, theta: float = 0.0, tau12: float = 
     return out
 
 
+def lbm_spectral_radius(lam: float, mu: float, theta: float = 0.0, tau12: float = 0.0,
+                        tau22: float = 0.0, nk: int = 50, nphi: int = 5) -> float:
+    """Sampled sup of the von Neumann spectral radius (<= 1: stable)."""
+    rho = ctypes.c_double()
+    st = _lib.lbm_spectral_radius(lam, mu, theta, tau12, tau22, nk, nphi, ctypes.byref(rho))
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_spectral_radius: invalid parameters")
+    return rho.value
+
+
 def lbm_reset(ctx: int) -> None:
     _check(_lib.lbm_reset(ctx), "lbm_reset")
 
@@ -260,8 +272,15 @@ class Lattice:
     """One periodic lattice (context) on the current CUDA device."""
 
     def __init__(self, nx: int, ny: int, lam: float, mu: float, dtype: str = "f32",
-                 theta: float = 0.0, tau12: float = 0.0, tau22: float = 0.0):
+                 theta: float = 0.0, tau12: float = 0.0, tau22: float = 0.0,
+                 check_stability: bool = False):
         self.nx, self.ny, self.dtype = int(nx), int(ny), dtype
+        if check_stability:
+            rho = lbm_spectral_radius(lam, mu, theta, tau12, tau22)
+            if rho > 1.0 + 1e-9:
+                import warnings
+                warnings.warn("lattice Boltzmann parameters are von Neumann unstable "
+                              "(spectral radius %.6f > 1)" % rho, RuntimeWarning)
         self.ctx = lbm_create_ex(self.nx, self.ny, float(lam), float(mu), DTYPES[dtype],
                                  theta, tau12, tau22)
 

@@ -63,3 +63,18 @@ def test_status_codes_match_header():
     txt = open(os.path.join(ROOT, "include", "lbm.h")).read()
     for name, val in re.findall(r"(LBM_(?:OK|ERR_[A-Z_]+))\s*=\s*(-?\d+)", txt):
         assert getattr(P, name) == int(val)
+
+
+def test_spectral_radius_matches_oracle_eigenvalues():
+    """The library's Gelfand-formula spectral radius agrees with the oracle's
+    numpy eigenvalues (Sec. 4 sampling)."""
+    import oracle
+    import oracle.fourier as F
+    for E, nu, t12, t22 in ((0.082, -0.4, 0.5, 0.5), (0.11, 0.8, 0.5, 0.5), (1.0, 0.3, 0.5, 0.5),
+                            (0.5, 0.2, 0.9, 0.3), (0.05, 0.999, 0.5, 0.5)):
+        lam, mu = oracle.lame_2d(E, nu)
+        ref = F.spectral_radius(oracle.relaxation_rates(lam, mu, tau12=t12, tau22=t22))
+        got = P.lbm_spectral_radius(lam, mu, 0.0, t12, t22)
+        assert abs(got - ref) < 1e-7 * ref, (E, nu, got, ref)
+    with pytest.raises(P.LBMError):
+        P.lbm_spectral_radius(0.3, -1.0)

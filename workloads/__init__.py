@@ -196,6 +196,52 @@ def fourth_order_field(n: int, lam: float, mu: float, A: float = 9e-4, B: float 
     return Manufactured(lam, mu, _pw(n, n, modes))
 
 
+GAUSS_SIGMA = (120.0 ** -0.5, 123.0 ** -0.5, 118.0 ** -0.5, 125.0 ** -0.5)  # Sec. 6.3.5 table
+
+
+def gaussian_hill(n: int, lam: float, mu: float, amp: float = 1e-3, sigma=GAUSS_SIGMA):
+    """The Gaussian-hill manufactured solution of Sec. 6.3.5 on the unit square
+    sampled by an n-by-n lattice:
+      u_x = amp exp(-(x~ - 1/2)^2 / s1^2) exp(-(y~ - 1/2)^2 / s2^2) - mean,
+      u_y = amp exp(-(x~ - 1/2)^2 / s3^2) exp(-(y~ - 1/2)^2 / s4^2) - mean,
+    the means being amp pi s_a s_b erf(1/(2 s_a)) erf(1/(2 s_b)).  The field is
+    periodic only approximately (it is ~1e-13 amp at the domain edge); the
+    lattice force g = (-mu lap u - K grad div u) / n^2 (unit-square derivatives,
+    E~ = 1 scaling of the moduli) has its small grid mean removed so that the
+    periodic problem has a steady state.  Returns (gx, gy, exact) with exact the
+    fields (5, n, n) [u_x, u_y, sigma_xx, sigma_yy, sigma_xy] in lattice units."""
+    from math import erf, pi, sqrt
+    s1, s2, s3, s4 = sigma
+    K = lam + mu
+    t = (np.arange(n, dtype=np.float64) + 0.5) / n - 0.5
+    X, Y = np.meshgrid(t, t)               # X varies along x (columns)
+
+    def hill(sa, sb):
+        G = amp * np.exp(-X * X / (sa * sa)) * np.exp(-Y * Y / (sb * sb))
+        gx_ = -2.0 * X / (sa * sa) * G
+        gy_ = -2.0 * Y / (sb * sb) * G
+        gxx = (4.0 * X * X / sa ** 4 - 2.0 / (sa * sa)) * G
+        gyy = (4.0 * Y * Y / sb ** 4 - 2.0 / (sb * sb)) * G
+        gxy = 4.0 * X * Y / (sa * sa * sb * sb) * G
+        mean = amp * pi * sa * sb * erf(1.0 / (2.0 * sa)) * erf(1.0 / (2.0 * sb))
+        return G - mean, gx_, gy_, gxx, gyy, gxy
+
+    ux, ux_x, ux_y, ux_xx, ux_yy, ux_xy = hill(s1, s2)
+    uy, uy_x, uy_y, uy_xx, uy_yy, uy_xy = hill(s3, s4)
+    bx = -mu * (ux_xx + ux_yy) - K * (ux_xx + uy_xy)
+    by = -mu * (uy_xx + uy_yy) - K * (ux_xy + uy_yy)
+    gx = bx / (n * n)
+    gy = by / (n * n)
+    gx -= gx.mean()
+    gy -= gy.mean()
+    div = ux_x + uy_y
+    sxx = K * div + mu * (2.0 * ux_x - div)
+    syy = K * div + mu * (2.0 * uy_y - div)
+    sxy = mu * (ux_y + uy_x)
+    exact = np.stack([ux, uy, sxx / n, syy / n, sxy / n])
+    return np.ascontiguousarray(gx), np.ascontiguousarray(gy), exact
+
+
 def random_force(nx: int, ny: int, n_modes: int, kmax: int, seed: int) -> PlaneWaves:
     """Body force made of ``n_modes`` random Fourier modes: integer wave numbers
     (kx, ky) uniform in [-kmax, kmax]^2 without (0, 0); per component amplitude
