@@ -138,6 +138,20 @@ def dist_setup():
     return ws, rank, local
 
 
+def replica_aggregate(dist, elapsed_ms: float, units: float, device="cpu"):
+    """Replicas only: each rank times its own copy of the workload.  Returns
+    (max elapsed ms over ranks, sum of units over ranks); without a process
+    group, the local values."""
+    import torch
+    if dist is None or not dist.is_initialized():
+        return elapsed_ms, units
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def make_force(n: int):
     pw = W.random_force(n, n, n_modes=16, kmax=8, seed=FORCE_SEED)
     return W.random_force_grid(pw)
@@ -278,11 +292,8 @@ def run_ours(args, ws, rank, local):
     res = time_variant(args, args.dtype, gx_d, gy_d, torch, P, args.steps, args.warmup)
     barrier()
     clocks = sampler.stop()
-    t = torch.tensor([res["total_ms"]], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    lups = float(n) * n * args.iters * args.steps * ws
+    total_ms, lups = replica_aggregate(dist if ws > 1 else None, res["total_ms"],
+                                       float(n) * n * args.iters * args.steps, device="cuda")
     value = lups / (total_ms / 1e3) / 1e6
     per_launch_s = res["iter_ms"] / 1e3 / (args.steps * args.iters)
     bpl = BYTES_PER_LUP[args.dtype] * n * n
