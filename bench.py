@@ -48,8 +48,8 @@ FORCE_SEED = 0x2208_14870
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32": {"bytes_per_launch": (671.151104e6 + 486.694144e6) * 16, "kernel_hash": "edb850198410e1fd"},
-    "f16s": {"bytes_per_launch": (536.964608e6 + 366.787840e6) * 16, "kernel_hash": "edb850198410e1fd"},
+    "f32": {"bytes_per_launch": (671.171072e6 + 486.934272e6) * 16, "kernel_hash": "234028f04f09fba8"},
+    "f16s": {"bytes_per_launch": (536.996352e6 + 367.842560e6) * 16, "kernel_hash": "234028f04f09fba8"},
 }
 
 

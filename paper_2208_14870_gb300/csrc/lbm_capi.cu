@@ -320,7 +320,10 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     c->rates.theta = theta;
     c->gen = !(c->rates.w12 == 1.0 && c->rates.w22 == 1.0);
     if (dtype == LBM_F64) c->V = nx >= 64 ? 2 : 1;
-    else c->V = nx >= 128 ? 4 : 1;
+    else {
+        const int vmax = dtype == LBM_F16S ? max_vec<S_F16S>() : max_vec<S_F32>();
+        c->V = nx >= 32 * vmax ? vmax : 1;
+    }
     {
         // persistent residual-check grid: resident blocks per SM x SMs
         int sms = 0;

@@ -20,10 +20,35 @@
 
 namespace lbm {
 
-constexpr int BY = 8;              // rows per block (block = 32 x BY threads)
-constexpr int kThreads = 32 * BY;
+// Launch shape (compile-time): rows per block, resident blocks per SM the
+// plain step is compiled for, and nodes per thread of the FP16-shifted wide
+// variant. The defaults are the fastest of a sweep at 16384^2 on GB300
+// (FP32: BY 8, 4 blocks, 4 nodes; FP16S: 4 blocks of 2 nodes beat 3 of 4).
+#ifndef LBM_BY
+#define LBM_BY 8
+#endif
+#ifndef LBM_MINB_F32
+#define LBM_MINB_F32 4
+#endif
+#ifndef LBM_MINB_F16S
+#define LBM_MINB_F16S 4
+#endif
+#ifndef LBM_F16S_V
+#define LBM_F16S_V 2
+#endif
+#ifndef LBM_MINB_F64
+#define LBM_MINB_F64 3
+#endif
+constexpr int BY = LBM_BY;         // rows per block (block = 32 x BY threads)
 
 enum Storage { S_F64 = 0, S_F32 = 1, S_F16S = 2 };
+
+// Nodes per thread (spaced 32 apart) of the wide step variant per storage.
+template <int S>
+constexpr int max_vec() {
+    return S == S_F64 ? 2 : (S == S_F16S ? LBM_F16S_V : 4);
+}
+constexpr int kThreads = 32 * BY;
 
 template <int S> struct StoreT;
 // T: collision arithmetic, P: stored population, G: stored force,
@@ -41,7 +66,7 @@ struct StepParams {
     int64_t plane;          // elements between planes
     const void* src;        // 8 population planes (storage type)
     void* dst;
-    const float* csrc;      // F16S: carrier planes m*_10, m*_01 (FP32, stride plane)
+    const float* csrc;      // F16S: carriers (m*_10, m*_01) interleaved per node (float2)
     float* cdst;
     const void* gx;         // force planes (G)
     const void* gy;
@@ -70,18 +95,20 @@ __device__ __forceinline__ void gather(const StepParams& a, int64_t r0, int64_t 
     const int64_t i0 = r0 + xm, i1 = rm + x, i2 = r0 + xp, i3 = rp + x;
     const int64_t i4 = rm + xm, i5 = rm + xp, i6 = rp + xp, i7 = rp + xm;
     if constexpr (S == S_F16S) {
+        // carriers interleaved per node: (m*_10, m*_01) as one float2
         const float hinv = a.hinv;
-        const float* c10 = a.csrc;
-        const float* c01 = a.csrc + pl;
+        const float2* c = reinterpret_cast<const float2*>(a.csrc);
         const float k1 = 0.5f * (1.0f - theta), k5 = 0.25f * theta;
-        f[0] = ld_h(s + 0 * pl + i0) * hinv + k1 * ldg(c10 + i0);
-        f[1] = ld_h(s + 1 * pl + i1) * hinv + k1 * ldg(c01 + i1);
-        f[2] = ld_h(s + 2 * pl + i2) * hinv - k1 * ldg(c10 + i2);
-        f[3] = ld_h(s + 3 * pl + i3) * hinv - k1 * ldg(c01 + i3);
-        f[4] = ld_h(s + 4 * pl + i4) * hinv + k5 * (ldg(c10 + i4) + ldg(c01 + i4));
-        f[5] = ld_h(s + 5 * pl + i5) * hinv + k5 * (ldg(c01 + i5) - ldg(c10 + i5));
-        f[6] = ld_h(s + 6 * pl + i6) * hinv - k5 * (ldg(c10 + i6) + ldg(c01 + i6));
-        f[7] = ld_h(s + 7 * pl + i7) * hinv + k5 * (ldg(c10 + i7) - ldg(c01 + i7));
+        const float2 c0 = ldg(c + i0), c1 = ldg(c + i1), c2 = ldg(c + i2), c3 = ldg(c + i3);
+        const float2 c4 = ldg(c + i4), c5 = ldg(c + i5), c6 = ldg(c + i6), c7 = ldg(c + i7);
+        f[0] = ld_h(s + 0 * pl + i0) * hinv + k1 * c0.x;
+        f[1] = ld_h(s + 1 * pl + i1) * hinv + k1 * c1.y;
+        f[2] = ld_h(s + 2 * pl + i2) * hinv - k1 * c2.x;
+        f[3] = ld_h(s + 3 * pl + i3) * hinv - k1 * c3.y;
+        f[4] = ld_h(s + 4 * pl + i4) * hinv + k5 * (c4.x + c4.y);
+        f[5] = ld_h(s + 5 * pl + i5) * hinv + k5 * (c5.y - c5.x);
+        f[6] = ld_h(s + 6 * pl + i6) * hinv - k5 * (c6.x + c6.y);
+        f[7] = ld_h(s + 7 * pl + i7) * hinv + k5 * (c7.x - c7.y);
     } else {
         (void)theta;
         f[0] = T(ldg(s + 0 * pl + i0));
@@ -115,8 +142,7 @@ __device__ __forceinline__ void store_f16s(const StepParams& a, int64_t idx, con
     }
     const float e10 = (r[0] - r[2]) + ((r[4] - r[6]) - (r[5] - r[7]));
     const float e01 = (r[1] - r[3]) + ((r[4] - r[6]) + (r[5] - r[7]));
-    a.cdst[idx] = m10s - e10;
-    a.cdst[pl + idx] = m01s - e01;
+    reinterpret_cast<float2*>(a.cdst)[idx] = make_float2(m10s - e10, m01s - e01);
 }
 
 // Store the post-collision state of node idx.
@@ -291,7 +317,7 @@ __device__ __forceinline__ void step_tile(const StepParams& a,
 }
 
 template <int S, int V, bool GEN, bool CHECK>
-__global__ void __launch_bounds__(kThreads, CHECK ? 2 : (S == S_F32 ? 4 : 3))
+__global__ void __launch_bounds__(kThreads, CHECK ? 2 : (S == S_F32 ? LBM_MINB_F32 : (S == S_F16S ? LBM_MINB_F16S : LBM_MINB_F64)))
 k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
     using U = typename StoreT<S>::U;
     const int ntx = (a.nx + 32 * V - 1) / (32 * V);

@@ -7,8 +7,6 @@
 
 namespace lbm {
 
-template <int S>
-constexpr int max_vec() { return S == S_F64 ? 2 : 4; }
 
 template <int S, int V>
 static void launch_step_v(const StepParams& a, const Coef<typename StoreT<S>::T>& c, bool gen,
