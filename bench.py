@@ -37,19 +37,22 @@ import workloads as W  # noqa: E402
 
 METRIC = "MLUPS and HBM GB/s (% of GB300 peak); solves/sec and p99 latency, batched vs plain"
 FALLBACK_HBM_GBS = 6800.0
-# Algorithmic bytes per lattice update (one node, one step): 8 populations
-# read + 8 written + 2 force components read; FP16-shifted adds the two FP32
-# first-moment carriers read and written.
-BYTES_PER_LUP = {"f64": 8 * 8 * 2 + 2 * 8, "f32": 8 * 4 * 2 + 2 * 4, "f16s": (8 * 2 + 2 * 4) * 2 + 2 * 4}
+# Algorithmic bytes per node and stream-collide launch: 8 populations read + 8
+# written + 2 force components read; FP16-shifted adds the two FP32
+# first-moment carriers read and written.  A launch advances one step, or two
+# (FP32 two-step kernel): bytes per lattice update = this / steps per launch.
+BYTES_PER_LAUNCH_NODE = {"f64": 8 * 8 * 2 + 2 * 8, "f32": 8 * 4 * 2 + 2 * 4, "f16s": (8 * 2 + 2 * 4) * 2 + 2 * 4}
 FORCE_SEED = 0x2208_14870
-# DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype,
+# DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype
+# and steps per launch,
 # with the hash of the kernel sources it was taken on (null once they change).
-# Captured on 4096^2 (profiles/k_step_*_4096_full.md) and scaled by the node
+# Captured on 4096^2 (profiles/k_step*_4096_full.md) and scaled by the node
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32": {"bytes_per_launch": (671.171072e6 + 486.934272e6) * 16, "kernel_hash": "234028f04f09fba8"},
-    "f16s": {"bytes_per_launch": (536.996352e6 + 367.842560e6) * 16, "kernel_hash": "234028f04f09fba8"},
+    "f32_x2": {"bytes_per_launch": (674.141440e6 + 489.935616e6) * 16, "kernel_hash": "6d20c5fddecf8f57"},
+    "f32_x1": {"bytes_per_launch": (671.171072e6 + 486.934272e6) * 16, "kernel_hash": "234028f04f09fba8"},
+    "f16s_x1": {"bytes_per_launch": (536.996352e6 + 367.842560e6) * 16, "kernel_hash": "234028f04f09fba8"},
 }
 
 
@@ -69,6 +72,7 @@ def kernel_hash() -> str:
     h.update(open(os.path.join(d, "lbm_core.cuh"), "rb").read())
     h.update(kernel_source(open(os.path.join(d, "lbm_kernels.cuh")).read()).encode())
     h.update(open(os.path.join(d, "lbm_ops.cuh"), "rb").read())
+    h.update(open(os.path.join(d, "lbm_step_f32.cu"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -203,7 +207,7 @@ def workload_config(args):
             "check_every": args.check_every, "E": 1.0, "nu": args.nu,
             "force": "16 modes, |kx|,|ky|<=8, amp N(0,1)/|k|^2, seed %#x" % FORCE_SEED,
             "l2": "inputs larger than L2: %.1f GB of populations and force read+written per launch, L2 129 MB" % (
-                args.n * args.n * BYTES_PER_LUP[args.dtype] / 1e9)}
+                args.n * args.n * BYTES_PER_LAUNCH_NODE[args.dtype] / 1e9)}
 
 
 def cpu_baseline(args):
@@ -226,11 +230,27 @@ def cpu_baseline(args):
 # Our arm
 # ---------------------------------------------------------------------------
 
-def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True):
+def launches_per_iterate(iters, check_every, spl):
+    """Stream-collide launches of lbm_iterate_checked(iters, check_every) from
+    step 0: each window is check_every - 1 plain steps (paired when two steps
+    run per launch) and the check step (the second of a pair)."""
+    def plain(m):
+        return m // 2 + m % 2 if spl == 2 else m
+    total, left = 0, iters
+    while left >= check_every:
+        total += plain(check_every - 2) + 1 if (spl == 2 and check_every >= 2) else plain(check_every - 1) + 1
+        left -= check_every
+    return total + plain(left)
+
+
+def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, spl=None):
     """Device-resident timing of `nsteps` benchmark steps; returns dict."""
     n = args.n
     lam, mu = W.lame_2d(1.0, args.nu)
     lat = P.Lattice(n, n, lam, mu, dtype)
+    if spl is not None:
+        lat.steps_per_launch = spl
+    spl = lat.steps_per_launch
     stream = torch.cuda.current_stream()
     lat.set_stream(stream.cuda_stream)
     lat.set_force(gx_d, gy_d)
@@ -261,8 +281,9 @@ def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True):
     iter_ms = sum(a.elapsed_time(b) for a, b in evs)
     lat.close()
     del out5
-    return {"total_ms": total_ms, "iter_ms": iter_ms, "steps": nsteps,
-            "launches": nsteps * (args.iters + 1)}
+    per_iter = launches_per_iterate(args.iters, args.check_every, spl)
+    return {"total_ms": total_ms, "iter_ms": iter_ms, "steps": nsteps, "spl": spl,
+            "step_launches": nsteps * per_iter, "launches": nsteps * (per_iter + 1)}
 
 
 def run_ours(args, ws, rank, local):
@@ -295,26 +316,31 @@ def run_ours(args, ws, rank, local):
     total_ms, lups = replica_aggregate(dist if ws > 1 else None, res["total_ms"],
                                        float(n) * n * args.iters * args.steps, device="cuda")
     value = lups / (total_ms / 1e3) / 1e6
-    per_launch_s = res["iter_ms"] / 1e3 / (args.steps * args.iters)
-    bpl = BYTES_PER_LUP[args.dtype] * n * n
+    spl = res["spl"]
+    per_launch_s = res["iter_ms"] / 1e3 / res["step_launches"]
+    # a launch reads and writes the populations once and reads the force once,
+    # whether it advances one step or two
+    bpl = BYTES_PER_LAUNCH_NODE[args.dtype] * n * n
     achieved = bpl / per_launch_s / 1e9
-    tr = NCU_TRAFFIC.get(args.dtype)
+    tr = NCU_TRAFFIC.get("%s_x%d" % (args.dtype, spl))
     traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_hash") == kernel_hash() else None
 
     variants = {}
     if not args.quick:
-        for dt in args.variants:
-            if dt == args.dtype:
+        for name in args.variants:
+            dt, _, k = name.partition("x")
+            if name == args.dtype or dt not in BYTES_PER_LAUNCH_NODE:
                 continue
-            r = time_variant(args, dt, gx_d, gy_d, torch, P, max(2, args.steps // 2), 2)
-            pl = r["iter_ms"] / 1e3 / (r["steps"] * args.iters)
-            variants[dt] = {
+            r = time_variant(args, dt, gx_d, gy_d, torch, P, max(2, args.steps // 2), 2,
+                             spl=int(k) if k else None)
+            pl = r["iter_ms"] / 1e3 / r["step_launches"]
+            b = BYTES_PER_LAUNCH_NODE[dt] * n * n
+            variants[name] = {
                 "value": float(n) * n * args.iters * r["steps"] / (r["total_ms"] / 1e3) / 1e6,
                 "unit": "MLUPS", "ms_per_step": r["total_ms"] / r["steps"],
-                "kernel_us": pl * 1e6,
-                "achieved_gbs": BYTES_PER_LUP[dt] * n * n / pl / 1e9,
-                "frac_of_measured_hbm": BYTES_PER_LUP[dt] * n * n / pl / 1e9 / peak,
-                "bytes_per_lup": BYTES_PER_LUP[dt]}
+                "steps_per_launch": r["spl"], "kernel_us": pl * 1e6,
+                "achieved_gbs": b / pl / 1e9, "frac_of_measured_hbm": b / pl / 1e9 / peak,
+                "bytes_per_lup": BYTES_PER_LAUNCH_NODE[dt] / r["spl"]}
 
     e2e = None
     if not args.no_e2e:
@@ -334,9 +360,11 @@ def run_ours(args, ws, rank, local):
             "config": workload_config(args),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_step<%s> (fused stream-collide)" % args.dtype,
-                         "kernel_us": per_launch_s * 1e6,
-                         "bytes_per_lup": BYTES_PER_LUP[args.dtype],
+                         "kernel": ("k_step2<%s> (two fused stream-collide steps per launch)" if spl == 2
+                                    else "k_step<%s> (fused stream-collide)") % args.dtype,
+                         "kernel_us": per_launch_s * 1e6, "steps_per_launch": spl,
+                         "bytes_per_launch_node": BYTES_PER_LAUNCH_NODE[args.dtype],
+                         "bytes_per_lup": BYTES_PER_LAUNCH_NODE[args.dtype] / spl,
                          "peak_kind": peak_kind + " copy bandwidth",
                          "frac_of_nominal_8tbs": achieved / 8000.0},
             "clocks": clocks,
@@ -513,7 +541,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--dtype", default="f32", choices=["f64", "f32", "f16s"])
     ap.add_argument("--nu", type=float, default=0.3)
-    ap.add_argument("--variants", nargs="*", default=["f16s"])
+    ap.add_argument("--variants", nargs="*", default=["f16s", "f32x1"],
+                    help="extra storage variants; a suffix xK fixes K steps per launch")
     ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)

@@ -116,6 +116,21 @@ void lbm_destroy(lbm_ctx *ctx);
  * all later work of this context.  The caller keeps ownership of the stream. */
 int lbm_set_stream(lbm_ctx *ctx, void *stream);
 
+/* Pseudo-time steps per stream-collide launch: 1 or 2.  With 2, one launch
+ * runs two consecutive steps of Algorithm 1 (Sec. 3.3, Eqs. collision and
+ * streaming): the first step's post-collision state of a tile and its one-node
+ * halo stays on chip, so the populations cross device memory once per two
+ * steps.  The arithmetic per node is unchanged and the state after every
+ * launch equals that of the same steps taken one per launch, bit for bit; a
+ * residual check (lbm_iterate_checked, lbm_solve) falls on the second step of
+ * a pair.  Available for LBM_F32 storage on lattices with nx >= 64 and
+ * ny >= 32, where it is the default; other contexts run one step per launch.
+ * Paper: the scheme advances one step at a time; the pairing is a schedule
+ * of the same steps, not part of the method.
+ * Errors: LBM_ERR_ARG (k not 1 or 2, or k = 2 where it is not available). */
+int lbm_set_steps_per_launch(lbm_ctx *ctx, int k);
+int lbm_get_steps_per_launch(lbm_ctx *ctx, int *k);
+
 /* Body force (constant in pseudo-time, Sec. 2.1).  gx, gy: host arrays of
  * nx*ny doubles (lattice units), copied.  The force must be finite; the
  * steady state exists for a zero-mean force (the mean of u is conserved,

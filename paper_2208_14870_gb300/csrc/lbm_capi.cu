@@ -1,6 +1,7 @@
 // lbm_capi.cu -- the C ABI of include/lbm.h: context lifetime, parameter
 // mapping (Table 1), host <-> device transfers and the pseudo-time driver
 // (iterate / solve) around the kernels of lbm_kernels.cuh.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -74,6 +75,8 @@ struct lbm_ctx {
     int V = 1;
     size_t bytes = 0;
     int64_t nblocks = 0;           // grid of the persistent residual-check launch
+    int spl = 1;                   // pseudo-time steps per stream-collide launch (1 or 2)
+    int64_t nblocks2 = 0;          // grid of the persistent two-step check launch
 };
 
 namespace {
@@ -134,6 +137,37 @@ cudaError_t launch_step(lbm_ctx* c, bool check) {
         c->step += 1;
     }
     return e;
+}
+
+// Two steps in one launch (FP32 storage, step2_fits); with check the second
+// step is the residual-check step.
+cudaError_t launch_step2(lbm_ctx* c, bool check) {
+    const StepParams a = params(c, c->cur);
+    cudaError_t e = step2_f32(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks2, c->stream);
+    if (e == cudaSuccess) {
+        c->cur ^= 1;
+        c->step += 2;
+    }
+    return e;
+}
+
+// n plain steps, paired into two-step launches where the context uses them.
+cudaError_t run_plain(lbm_ctx* c, int64_t n) {
+    cudaError_t e = cudaSuccess;
+    if (c->spl == 2)
+        for (; n >= 2 && e == cudaSuccess; n -= 2) e = launch_step2(c, false);
+    for (; n > 0 && e == cudaSuccess; --n) e = launch_step(c, false);
+    return e;
+}
+
+// to_check - 1 plain steps followed by the residual-check step.
+cudaError_t run_window(lbm_ctx* c, int64_t to_check) {
+    if (c->spl == 2 && to_check >= 2) {
+        cudaError_t e = run_plain(c, to_check - 2);
+        return e == cudaSuccess ? launch_step2(c, true) : e;
+    }
+    cudaError_t e = run_plain(c, to_check - 1);
+    return e == cudaSuccess ? launch_step(c, true) : e;
 }
 
 cudaError_t launch_fields(lbm_ctx* c, double* out) {
@@ -335,6 +369,12 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
         const int64_t tiles = step_tiles(nx, ny, c->V);
         c->nblocks = (int64_t)sms * occ;
         if (c->nblocks > tiles) c->nblocks = tiles;
+        if (dtype == LBM_F32 && step2_fits(nx, ny)) {
+            c->spl = 2;
+            const int64_t tiles2 = step2_tiles(nx, ny);
+            c->nblocks2 = (int64_t)sms * step2_check_occupancy(c->gen);
+            if (c->nblocks2 > tiles2) c->nblocks2 = tiles2;
+        }
         e = cudaSuccess;
     }
 
@@ -354,7 +394,8 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     if (e == cudaSuccess) e = alloc(&c->force, fb);
     const size_t snap_bytes = (dtype == LBM_F64 ? sizeof(double) : sizeof(float)) * 2 * c->n;
     if (e == cudaSuccess) e = alloc(&c->snap, snap_bytes);
-    if (e == cudaSuccess) e = alloc((void**)&c->partials, sizeof(double) * kRes * c->nblocks);
+    if (e == cudaSuccess) e = alloc((void**)&c->partials,
+                                       sizeof(double) * kRes * std::max(c->nblocks, c->nblocks2));
     if (e == cudaSuccess) e = alloc((void**)&c->counter, sizeof(unsigned int));
     if (e == cudaSuccess) e = alloc((void**)&c->result, sizeof(double) * kRes);
     if (e == cudaSuccess) e = alloc((void**)&c->absmax, sizeof(unsigned long long));
@@ -390,6 +431,26 @@ void lbm_destroy(lbm_ctx* c) {
     free_all(c);
     if (dev >= 0 && dev != c->device) cudaSetDevice(dev);
     delete c;
+}
+
+int lbm_set_steps_per_launch(lbm_ctx* c, int k) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (k != 1 && k != 2) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: k must be 1 or 2");
+    if (k == 2 && !(c->dtype == LBM_F32 && step2_fits(c->nx, c->ny)))
+        return fail(LBM_ERR_ARG,
+                    "lbm_set_steps_per_launch: two steps per launch need FP32 storage, nx >= 64 and ny >= 32");
+    if (k == 2 && c->nblocks2 == 0) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: not set up");
+    c->spl = k;
+    return LBM_OK;
+}
+
+int lbm_get_steps_per_launch(lbm_ctx* c, int* k) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!k) return fail(LBM_ERR_ARG, "lbm_get_steps_per_launch: null pointer");
+    *k = c->spl;
+    return LBM_OK;
 }
 
 int lbm_set_stream(lbm_ctx* c, void* stream) {
@@ -508,10 +569,8 @@ int lbm_iterate(lbm_ctx* c, int64_t n) {
     if (rc) return rc;
     if (n < 0) return fail(LBM_ERR_ARG, "lbm_iterate: n must be >= 0");
     if (n > 0) c->state_zero = false;
-    for (int64_t i = 0; i < n; ++i) {
-        cudaError_t e = launch_step(c, false);
-        if (e != cudaSuccess) return cuda_fail(e, "lbm_iterate: step launch");
-    }
+    cudaError_t e = run_plain(c, n);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_iterate: step launch");
     return LBM_OK;
 }
 
@@ -522,16 +581,21 @@ int lbm_iterate_checked(lbm_ctx* c, int64_t n, int check_every, double* out) {
     if (n > 0) c->state_zero = false;
     int64_t last_window = 0;
     bool any = false;
-    for (int64_t i = 0; i < n; ++i) {
-        const bool check = ((c->step + 1) % check_every) == 0;
-        cudaError_t e = launch_step(c, check);
-        if (e != cudaSuccess) return cuda_fail(e, "lbm_iterate_checked: step launch");
-        if (check) {
-            last_window = c->snap_valid ? c->step - c->snap_step : 0;
-            any = c->snap_valid;
-            c->snap_valid = true;
-            c->snap_step = c->step;
+    // a check on every step whose index + 1 is a multiple of check_every
+    for (int64_t left = n; left > 0;) {
+        const int64_t to_check = check_every - (c->step % check_every);
+        if (to_check > left) {
+            cudaError_t e = run_plain(c, left);
+            if (e != cudaSuccess) return cuda_fail(e, "lbm_iterate_checked: step launch");
+            break;
         }
+        cudaError_t e = run_window(c, to_check);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_iterate_checked: step launch");
+        left -= to_check;
+        last_window = c->snap_valid ? c->step - c->snap_step : 0;
+        any = c->snap_valid;
+        c->snap_valid = true;
+        c->snap_step = c->step;
     }
     if (out) {
         double raw[kRes];
@@ -560,17 +624,14 @@ int lbm_solve(lbm_ctx* c, double tol, int64_t max_iters, int check_every, int64_
     int status = LBM_ERR_NOT_CONVERGED;
     while (done < max_iters) {
         const int64_t to_check = check_every - (c->step % check_every);
-        const int64_t plain = to_check - 1;
         if (done + to_check > max_iters) {
             rc = lbm_iterate(c, max_iters - done);
             if (rc) return rc;
             done = max_iters;
             break;
         }
-        rc = lbm_iterate(c, plain);
-        if (rc) return rc;
-        cudaError_t e = launch_step(c, true);
-        if (e != cudaSuccess) return cuda_fail(e, "lbm_solve: check launch");
+        cudaError_t e = run_window(c, to_check);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_solve: step launch");
         done += to_check;
         double raw[kRes], res[kRes];
         rc = read_residual(c, raw);

@@ -14,6 +14,17 @@
 
 namespace lbm {
 
+// Rounding is spelled out wherever it could depend on the compiler: a
+// product that is not exact is either rounded on its own (rmul, never fused
+// into a later add) or fused on purpose (fmad).  Products with 1/2, 1/4 and 2
+// are exact, so fusing them or not gives the same bits.  Every kernel that
+// runs this arithmetic (one step per launch, two steps per launch, the
+// batched arena) therefore computes the same bits for the same inputs.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
+
 // Moments of the collision basis.
 template <typename T>
 struct Mom {
@@ -68,16 +79,16 @@ __device__ __forceinline__ Mom<T> collide(const Mom<T>& m, T gx, T gy, const Coe
     v = m.m01 + T(0.5) * gy;
     s.m10 = m.m10 + gx;
     s.m01 = m.m01 + gy;
-    s.m11 = c.a11 * m.m11;
-    s.ms = c.as * m.ms;
-    s.md = c.ad * m.md;
+    s.m11 = rmul(c.a11, m.m11);
+    s.ms = rmul(c.as, m.ms);
+    s.md = rmul(c.ad, m.md);
     if (GEN) {
-        s.m12 = c.w12t * u + c.a12 * m.m12;
-        s.m21 = c.w21t * v + c.a21 * m.m21;
-        s.m22 = c.a22 * m.m22;
+        s.m12 = fmad(c.w12t, u, rmul(c.a12, m.m12));
+        s.m21 = fmad(c.w21t, v, rmul(c.a21, m.m21));
+        s.m22 = rmul(c.a22, m.m22);
     } else {
-        s.m12 = c.theta * u;
-        s.m21 = c.theta * v;
+        s.m12 = rmul(c.theta, u);
+        s.m21 = rmul(c.theta, v);
         s.m22 = T(0);
     }
     return s;
@@ -118,8 +129,8 @@ __device__ __forceinline__ Mom<T> deviation_moments(const Mom<T>& s, T theta) {
     Mom<T> n = s;
     n.m10 = T(0);
     n.m01 = T(0);
-    n.m12 = s.m12 - theta * s.m10;
-    n.m21 = s.m21 - theta * s.m01;
+    n.m12 = fmad(-theta, s.m10, s.m12);
+    n.m21 = fmad(-theta, s.m01, s.m21);
     return n;
 }
 

@@ -101,14 +101,15 @@ __device__ __forceinline__ void gather(const StepParams& a, int64_t r0, int64_t 
         const float k1 = 0.5f * (1.0f - theta), k5 = 0.25f * theta;
         const float2 c0 = ldg(c + i0), c1 = ldg(c + i1), c2 = ldg(c + i2), c3 = ldg(c + i3);
         const float2 c4 = ldg(c + i4), c5 = ldg(c + i5), c6 = ldg(c + i6), c7 = ldg(c + i7);
-        f[0] = ld_h(s + 0 * pl + i0) * hinv + k1 * c0.x;
-        f[1] = ld_h(s + 1 * pl + i1) * hinv + k1 * c1.y;
-        f[2] = ld_h(s + 2 * pl + i2) * hinv - k1 * c2.x;
-        f[3] = ld_h(s + 3 * pl + i3) * hinv - k1 * c3.y;
-        f[4] = ld_h(s + 4 * pl + i4) * hinv + k5 * (c4.x + c4.y);
-        f[5] = ld_h(s + 5 * pl + i5) * hinv + k5 * (c5.y - c5.x);
-        f[6] = ld_h(s + 6 * pl + i6) * hinv - k5 * (c6.x + c6.y);
-        f[7] = ld_h(s + 7 * pl + i7) * hinv + k5 * (c7.x - c7.y);
+        // (the FP16 value times the power-of-two 1/scale is exact)
+        f[0] = fmad(k1, c0.x, ld_h(s + 0 * pl + i0) * hinv);
+        f[1] = fmad(k1, c1.y, ld_h(s + 1 * pl + i1) * hinv);
+        f[2] = fmad(-k1, c2.x, ld_h(s + 2 * pl + i2) * hinv);
+        f[3] = fmad(-k1, c3.y, ld_h(s + 3 * pl + i3) * hinv);
+        f[4] = fmad(k5, c4.x + c4.y, ld_h(s + 4 * pl + i4) * hinv);
+        f[5] = fmad(k5, c5.y - c5.x, ld_h(s + 5 * pl + i5) * hinv);
+        f[6] = fmad(-k5, c6.x + c6.y, ld_h(s + 6 * pl + i6) * hinv);
+        f[7] = fmad(k5, c7.x - c7.y, ld_h(s + 7 * pl + i7) * hinv);
     } else {
         (void)theta;
         f[0] = T(ldg(s + 0 * pl + i0));
@@ -330,6 +331,149 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
     if (CHECK) residual_reduce<U>(a, acc);
 }
 
+// ---------------------------------------------------------------------------
+// Two pseudo-time steps per launch, FP32 storage (temporal blocking).
+//
+// A block of 256 threads (8 warps) owns one output tile of kT2OX x kT2OY
+// nodes and a slot array of kT2W x kT2H nodes: the tile grown by one node on
+// every side.  Step 1 pulls the stored f*(t) from global memory exactly as
+// the single step does, collides every slot and keeps f*(t+1) of all slots in
+// shared memory; step 2 pulls f*(t+1) of the tile's nodes from shared memory
+// (their pull neighbours are the halo slots), collides again and stores
+// f*(t+2) of the tile.  The state crosses HBM once per two steps: per node and
+// launch 32 bytes read, 32 written and 8 of force read, i.e. 36 bytes per
+// lattice update instead of 72.  Thread (lane, warp) owns slot columns lane
+// and lane + 32 and slot rows warp + 8k in both steps, so the force it loaded
+// in step 1 serves step 2 from registers.  The per-node arithmetic is the
+// single step's (gather, collide, populations on the same FP32 values), so a
+// launch reproduces two single-step launches exactly.
+//
+// The halo wraps at most once, which needs nx >= kT2W and ny >= kT2H
+// (step2_fits).  CHECK makes the second step the residual-check step of
+// k_step<..., CHECK> (snapshot compared with u^{t+1}, the second step's input
+// state) and is launched as a persistent grid; the plain variant has one
+// block per tile.
+#ifndef LBM_T2_RPW
+#define LBM_T2_RPW 4
+#endif
+#ifndef LBM_MINB_T2
+#define LBM_MINB_T2 3
+#endif
+constexpr int kT2Rows = LBM_T2_RPW;             // slot rows per warp
+constexpr int kT2W = 64;                        // slot columns (two per lane)
+constexpr int kT2H = 8 * kT2Rows;               // slot rows
+constexpr int kT2OX = kT2W - 2, kT2OY = kT2H - 2;
+constexpr int kT2Threads = 256;
+constexpr int kT2Smem = 8 * kT2H * kT2W * (int)sizeof(float);
+static_assert(kT2Threads == kThreads, "residual_reduce sizes its scratch by kThreads");
+
+template <bool GEN, bool CHECK>
+__device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float>& c, float* sm,
+                                           int tx, int ty, float acc[kRes]) {
+    constexpr int PL = kT2H * kT2W;             // shared-memory plane
+    const int nx = a.nx, ny = a.ny;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = tx * kT2OX - 1, y0 = ty * kT2OY - 1;   // node of slot (0, 0)
+    const float* __restrict__ gxp = static_cast<const float*>(a.gx);
+    const float* __restrict__ gyp = static_cast<const float*>(a.gy);
+    int X[2], XM[2], XP[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        int x = x0 + lane + 32 * j;
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+        X[j] = x;
+        XM[j] = wrap_dec(x, nx);
+        XP[j] = wrap_inc(x, nx);
+    }
+    float gx[kT2Rows][2], gy[kT2Rows][2];
+    // Step 1: f*(t+1) of every slot into shared memory.
+#pragma unroll
+    for (int k = 0; k < kT2Rows; ++k) {
+        const int r = warp + 8 * k;
+        int y = y0 + r;
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        const int64_t r0 = (int64_t)y * nx;
+        const int64_t rm = (int64_t)wrap_dec(y, ny) * nx, rp = (int64_t)wrap_inc(y, ny) * nx;
+        float f[2][8];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            gather<S_F32>(a, r0, rm, rp, X[j], XM[j], XP[j], f[j], c.theta);
+            gx[k][j] = ldg(gxp + r0 + X[j]);
+            gy[k][j] = ldg(gyp + r0 + X[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float u, v, fs[8];
+            populations(collide<float, GEN>(moments(f[j]), gx[k][j], gy[k][j], c, u, v), fs);
+            float* s = sm + r * kT2W + lane + 32 * j;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) s[p * PL] = fs[p];
+        }
+    }
+    __syncthreads();
+    // Step 2: the tile's nodes pull f*(t+1) from shared memory.
+    float* __restrict__ d = static_cast<float*>(a.dst);
+    float* __restrict__ snap = static_cast<float*>(a.snap);
+    const int64_t pl = a.plane, n = (int64_t)nx * ny;
+#pragma unroll
+    for (int k = 0; k < kT2Rows; ++k) {
+        const int r = warp + 8 * k;
+        const int y = y0 + r;
+        if (r < 1 || r > kT2H - 2 || y >= ny) continue;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int col = lane + 32 * j;
+            const int x = x0 + col;
+            if (col < 1 || col > kT2W - 2 || x >= nx) continue;
+            const int64_t idx = (int64_t)y * nx + x;
+            float so0 = 0.0f, so1 = 0.0f;
+            if (CHECK) {
+                so0 = snap[idx];
+                so1 = snap[n + idx];
+            }
+            const float* s = sm + r * kT2W + col;
+            float f[8];
+            f[0] = s[0 * PL - 1];               // f_p(x) = f*_p(x - c_p)
+            f[1] = s[1 * PL - kT2W];
+            f[2] = s[2 * PL + 1];
+            f[3] = s[3 * PL + kT2W];
+            f[4] = s[4 * PL - kT2W - 1];
+            f[5] = s[5 * PL - kT2W + 1];
+            f[6] = s[6 * PL + kT2W + 1];
+            f[7] = s[7 * PL + kT2W - 1];
+            float u, v, fs[8];
+            populations(collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), fs);
+#pragma unroll
+            for (int p = 0; p < 8; ++p) d[p * pl + idx] = fs[p];
+            if (CHECK) {
+                snap[idx] = u;
+                snap[n + idx] = v;
+                const float du = u - so0, dv = v - so1;
+                acc[0] = fmaxf(acc[0], fmaxf(fabsf(du), fabsf(dv)));
+                acc[1] = fmaxf(acc[1], fmaxf(fabsf(u), fabsf(v)));
+                acc[2] += du * du + dv * dv;
+                acc[3] += u * u + v * v;
+                if (!(isfinite(u) && isfinite(v))) acc[4] = 1.0f;
+            }
+        }
+    }
+}
+
+template <bool GEN, bool CHECK>
+__global__ void __launch_bounds__(kT2Threads, CHECK ? 2 : LBM_MINB_T2)
+k_step2(const StepParams a, const Coef<float> c) {
+    extern __shared__ float t2_smem[];
+    const int ntx = (a.nx + kT2OX - 1) / kT2OX;
+    const int64_t ntiles = (int64_t)ntx * ((a.ny + kT2OY - 1) / kT2OY);
+    float acc[kRes] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
+        step2_tile<GEN, CHECK>(a, c, t2_smem, tx, ty, acc);
+        if (t + gridDim.x < ntiles) __syncthreads();   // slots are reused by the next tile
+    }
+    if (CHECK) residual_reduce<float>(a, acc);
+}
+
 // Solution fields of the current state (Table 2, Eq. compute_bared), FP64:
 // out planes u_x, u_y, sigma_xx, sigma_yy, sigma_xy (stride nx*ny).
 template <int S>
@@ -483,6 +627,19 @@ inline int check_period(int dtype, double tol, int k) {
 inline int64_t step_tiles(int nx, int ny, int V) {
     return (int64_t)((nx + 32 * V - 1) / (32 * V)) * ((ny + BY - 1) / BY);
 }
+
+// Two-step launches (FP32): lattice large enough for a halo that wraps once.
+inline bool step2_fits(int nx, int ny) { return nx >= kT2W && ny >= kT2H; }
+
+inline int64_t step2_tiles(int nx, int ny) {
+    return (int64_t)((nx + kT2OX - 1) / kT2OX) * ((ny + kT2OY - 1) / kT2OY);
+}
+
+// Two fused steps of FP32 storage (k_step2); defined with the FP32 kernels.
+cudaError_t step2_f32(const StepParams& a, const Coef<float>& c, bool gen, bool check,
+                      int check_blocks, cudaStream_t st);
+// resident blocks per SM of the two-step CHECK kernel
+int step2_check_occupancy(bool gen);
 
 inline dim3 step_grid(int nx, int ny, int V) {
     return dim3((unsigned)((nx + 32 * V - 1) / (32 * V)), (unsigned)((ny + BY - 1) / BY));

@@ -57,6 +57,8 @@ _SIGS = {
                                  _c.POINTER(lbm_options), _c.POINTER(_vp)]),
     "lbm_destroy": (None, [_vp]),
     "lbm_set_stream": (_c.c_int, [_vp, _vp]),
+    "lbm_set_steps_per_launch": (_c.c_int, [_vp, _c.c_int]),
+    "lbm_get_steps_per_launch": (_c.c_int, [_vp, _c.POINTER(_c.c_int)]),
     "lbm_set_force": (_c.c_int, [_vp, _vp, _vp]),
     "lbm_set_force_device": (_c.c_int, [_vp, _vp, _vp]),
     "lbm_set_force_corrected": (_c.c_int, [_vp, _vp, _vp, _vp]),
@@ -142,6 +144,16 @@ def lbm_destroy(ctx: int) -> None:
 
 def lbm_set_stream(ctx: int, stream: int) -> None:
     _check(_lib.lbm_set_stream(ctx, stream), "lbm_set_stream")
+
+
+def lbm_set_steps_per_launch(ctx: int, k: int) -> None:
+    _check(_lib.lbm_set_steps_per_launch(ctx, k), "lbm_set_steps_per_launch")
+
+
+def lbm_get_steps_per_launch(ctx: int) -> int:
+    k = _c.c_int()
+    _check(_lib.lbm_get_steps_per_launch(ctx, _c.byref(k)), "lbm_get_steps_per_launch")
+    return k.value
 
 
 def lbm_set_force(ctx: int, gx_ptr: int, gy_ptr: int) -> None:
@@ -371,6 +383,14 @@ class Lattice:
     @property
     def step(self) -> int:
         return lbm_get_step(self.ctx)
+
+    @property
+    def steps_per_launch(self) -> int:
+        return lbm_get_steps_per_launch(self.ctx)
+
+    @steps_per_launch.setter
+    def steps_per_launch(self, k: int):
+        lbm_set_steps_per_launch(self.ctx, k)
 
     @property
     def rates(self) -> dict:

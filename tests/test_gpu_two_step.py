@@ -1,0 +1,109 @@
+"""Two pseudo-time steps per launch (FP32 storage): the fused launch runs the
+same per-node arithmetic as two single-step launches, so the state must agree
+bit for bit with one step per launch, on ragged tiles, with general rates,
+across residual-check windows, and through lbm_solve."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2208_14870_gb300 as P  # noqa: E402
+from paper_2208_14870_gb300 import Lattice  # noqa: E402
+
+
+def _pair(nx, ny, seed=1, **kw):
+    lam, mu = W.lame_2d(1.0, 0.3)
+    pw = W.random_force(nx, ny, 8, 4, seed=seed)
+    gx, gy = W.random_force_grid(pw)
+    a = Lattice(nx, ny, lam, mu, "f32", **kw)
+    b = Lattice(nx, ny, lam, mu, "f32", **kw)
+    for lat in (a, b):
+        lat.set_force(gx, gy)
+    a.steps_per_launch = 1
+    assert b.steps_per_launch == 2
+    return a, b, gx, gy, lam, mu
+
+
+# (64, 32) is the smallest lattice with two steps per launch; the others leave
+# ragged tiles in x and/or y (tile 62 x 30 nodes).
+@pytest.mark.parametrize("nx,ny", [(64, 32), (130, 70), (200, 97), (64, 300), (517, 33)])
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_two_step_launch_is_bit_identical(nx, ny, steps):
+    a, b, *_ = _pair(nx, ny)
+    with a, b:
+        a.iterate(steps)
+        b.iterate(steps)
+        assert a.step == b.step == steps
+        fa, fb = a.populations(), b.populations()
+        assert np.array_equal(fa, fb), float(np.max(np.abs(fa - fb)))
+
+
+@pytest.mark.parametrize("kw", [dict(tau12=0.9, tau22=0.3), dict(theta=0.25)])
+def test_two_step_general_rates_bit_identical(kw):
+    a, b, *_ = _pair(150, 61, seed=2, **kw)
+    with a, b:
+        a.iterate(9)
+        b.iterate(9)
+        assert np.array_equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("check_every", [2, 7, 10])
+def test_two_step_checked_windows(check_every):
+    """Residual checks fall on the same steps and see the same maxima; the
+    sums are reduced in another order (relative 1e-6)."""
+    a, b, *_ = _pair(128, 96, seed=3)
+    with a, b:
+        ra = a.iterate_checked(41, check_every)
+        rb = b.iterate_checked(41, check_every)
+        assert np.array_equal(a.populations(), b.populations())
+        assert ra[0] == rb[0] and ra[2] == rb[2] and ra[4] == rb[4]
+        assert abs(ra[1] - rb[1]) <= 1e-6 * abs(ra[1]) and abs(ra[3] - rb[3]) <= 1e-6 * ra[3]
+
+
+def test_two_step_solve_matches_single_step():
+    a, b, *_ = _pair(96, 64, seed=4)
+    with a, b:
+        sa = a.solve(1e-6, 200000, 100)
+        sb = b.solve(1e-6, 200000, 100)
+        assert sa == sb, (sa, sb)
+        assert np.array_equal(a.fields(), b.fields())
+
+
+def test_two_step_matches_oracle():
+    lam, mu = W.lame_2d(1.0, 0.3)
+    rates = oracle.relaxation_rates(lam, mu)
+    nx, ny = 140, 71
+    pw = W.random_force(nx, ny, 6, 4, seed=5)
+    gx, gy = W.random_force_grid(pw)
+    ref = oracle.run(oracle.zero_state(nx, ny), gx, gy, rates, 6)
+    with Lattice(nx, ny, lam, mu, "f32") as lat:
+        assert lat.steps_per_launch == 2
+        lat.set_force(gx, gy)
+        lat.iterate(6)
+        got, want = lat.fields(), oracle.fields(ref, gx, gy, rates)
+        err = max(float(np.max(np.abs(got[i] - want[i]))) / float(np.max(np.abs(want[i])))
+                  for i in range(5))
+        assert err < 2e-6, err
+
+
+def test_steps_per_launch_availability():
+    lam, mu = W.lame_2d(1.0, 0.3)
+    for nx, ny, dt, want in ((64, 32, "f32", 2), (63, 32, "f32", 1), (64, 31, "f32", 1),
+                             (256, 256, "f64", 1), (256, 256, "f16s", 1)):
+        with Lattice(nx, ny, lam, mu, dt) as lat:
+            assert lat.steps_per_launch == want, (nx, ny, dt)
+            lat.steps_per_launch = 1
+            if want == 1:
+                with pytest.raises(P.LBMError):
+                    lat.steps_per_launch = 2
+            else:
+                lat.steps_per_launch = 2
+            with pytest.raises(P.LBMError):
+                lat.steps_per_launch = 3
