@@ -50,9 +50,9 @@ FORCE_SEED = 0x2208_14870
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32_x2": {"bytes_per_launch": (674.141440e6 + 489.935616e6) * 16, "kernel_hash": "6d20c5fddecf8f57"},
+    "f32_x2": {"bytes_per_launch": (674.806016e6 + 494.653952e6) * 16, "kernel_hash": "088c5c35f9c159e2"},
     "f32_x1": {"bytes_per_launch": (671.171072e6 + 486.934272e6) * 16, "kernel_hash": "234028f04f09fba8"},
-    "f16s_x1": {"bytes_per_launch": (536.996352e6 + 367.842560e6) * 16, "kernel_hash": "234028f04f09fba8"},
+    "f16s_x1": {"bytes_per_launch": (536.991232e6 + 367.842816e6) * 16, "kernel_hash": "088c5c35f9c159e2"},
 }
 
 

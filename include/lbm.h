@@ -124,7 +124,7 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
  * launch equals that of the same steps taken one per launch, bit for bit; a
  * residual check (lbm_iterate_checked, lbm_solve) falls on the second step of
  * a pair.  Available for LBM_F32 storage on lattices with nx >= 64 and
- * ny >= 32, where it is the default; other contexts run one step per launch.
+ * ny >= 24, where it is the default; other contexts run one step per launch.
  * Paper: the scheme advances one step at a time; the pairing is a schedule
  * of the same steps, not part of the method.
  * Errors: LBM_ERR_ARG (k not 1 or 2, or k = 2 where it is not available). */

@@ -74,9 +74,9 @@ struct lbm_ctx {
     bool state_zero = true;        // state is the zero state (create / reset)
     int V = 1;
     size_t bytes = 0;
-    int64_t nblocks = 0;           // grid of the persistent residual-check launch
+    int64_t nblocks = 0;           // grid of the residual-check launch
     int spl = 1;                   // pseudo-time steps per stream-collide launch (1 or 2)
-    int64_t nblocks2 = 0;          // grid of the persistent two-step check launch
+    int64_t nblocks2 = 0;          // grid of the two-step check launch
 };
 
 namespace {
@@ -358,24 +358,11 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
         const int vmax = dtype == LBM_F16S ? max_vec<S_F16S>() : max_vec<S_F32>();
         c->V = nx >= 32 * vmax ? vmax : 1;
     }
-    {
-        // persistent residual-check grid: resident blocks per SM x SMs
-        int sms = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-        if (e != cudaSuccess || sms < 1) sms = 1;
-        int occ = dtype == LBM_F64 ? Ops<S_F64>::check_occupancy(c->V, c->gen)
-                : dtype == LBM_F32 ? Ops<S_F32>::check_occupancy(c->V, c->gen)
-                                   : Ops<S_F16S>::check_occupancy(c->V, c->gen);
-        const int64_t tiles = step_tiles(nx, ny, c->V);
-        c->nblocks = (int64_t)sms * occ;
-        if (c->nblocks > tiles) c->nblocks = tiles;
-        if (dtype == LBM_F32 && step2_fits(nx, ny)) {
-            c->spl = 2;
-            const int64_t tiles2 = step2_tiles(nx, ny);
-            c->nblocks2 = (int64_t)sms * step2_check_occupancy(c->gen);
-            if (c->nblocks2 > tiles2) c->nblocks2 = tiles2;
-        }
-        e = cudaSuccess;
+    // residual-check grids: one block per tile up to kMaxCheckBlocks
+    c->nblocks = std::min(step_tiles(nx, ny, c->V), kMaxCheckBlocks);
+    if (dtype == LBM_F32 && step2_fits(nx, ny)) {
+        c->spl = 2;
+        c->nblocks2 = std::min(step2_tiles(nx, ny), kMaxCheckBlocks);
     }
 
     const size_t pb = pop_elem_bytes(dtype) * 8 * c->plane;
@@ -439,7 +426,7 @@ int lbm_set_steps_per_launch(lbm_ctx* c, int k) {
     if (k != 1 && k != 2) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: k must be 1 or 2");
     if (k == 2 && !(c->dtype == LBM_F32 && step2_fits(c->nx, c->ny)))
         return fail(LBM_ERR_ARG,
-                    "lbm_set_steps_per_launch: two steps per launch need FP32 storage, nx >= 64 and ny >= 32");
+                    "lbm_set_steps_per_launch: two steps per launch need FP32 storage, nx >= 64 and ny >= 24");
     if (k == 2 && c->nblocks2 == 0) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: not set up");
     c->spl = k;
     return LBM_OK;

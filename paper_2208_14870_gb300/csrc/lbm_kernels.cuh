@@ -211,8 +211,26 @@ __device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) 
     __syncthreads();
     if (!is_last) return;
     __threadfence();
+    // (four blocks' partials in flight per thread: the grid may have 10^5 blocks)
     double w[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (unsigned int b = tid; b < nblocks; b += blockDim.x * blockDim.y) {
+    const unsigned int nthr = blockDim.x * blockDim.y;
+    unsigned int b = tid;
+    for (; b + 3 * nthr < nblocks; b += 4 * nthr) {
+        double q[4][kRes];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < kRes; ++k) q[u][k] = __ldcg(a.partials + (int64_t)(b + u * nthr) * kRes + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            w[0] = fmax(w[0], q[u][0]);
+            w[1] = fmax(w[1], q[u][1]);
+            w[2] += q[u][2];
+            w[3] += q[u][3];
+            w[4] = fmax(w[4], q[u][4]);
+        }
+    }
+    for (; b < nblocks; b += nthr) {
         const double* p = a.partials + (int64_t)b * kRes;
         w[0] = fmax(w[0], __ldcg(p + 0));
         w[1] = fmax(w[1], __ldcg(p + 1));
@@ -251,11 +269,12 @@ __device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) 
 //
 // The lattice is cut into tiles of 32*V columns by BY rows; block b handles
 // tiles b, b + gridDim.x, ...  The plain step is launched with one block per
-// tile.  CHECK adds the steady-state residual and is launched as a persistent
-// grid (a few blocks per SM): u^t (the displacement of this step's input
-// state) is compared with the snapshot taken at the previous check, the
-// snapshot is overwritten with u^t, and each block reduces its partials once,
-// after all of its tiles (FP64 across warps, blocks and the grid).
+// tile.  CHECK adds the steady-state residual: u^t (the displacement of this
+// step's input state) is compared with the snapshot taken at the previous
+// check, the snapshot is overwritten with u^t, and each block reduces its
+// partials once, after all of its tiles (FP64 across warps, blocks and the
+// grid).  The library launches it with one block per tile up to
+// kMaxCheckBlocks blocks (more tiles per block beyond that).
 // One tile of one step: tile (tx, ty) covers columns tx*32V .. tx*32V+32V-1
 // and rows ty*BY .. ty*BY+BY-1.  With CHECK the thread's residual partials
 // are accumulated into acc (snapshot type U).
@@ -335,8 +354,8 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
 // Two pseudo-time steps per launch, FP32 storage (temporal blocking).
 //
 // A block of 256 threads (8 warps) owns one output tile of kT2OX x kT2OY
-// nodes and a slot array of kT2W x kT2H nodes: the tile grown by one node on
-// every side.  Step 1 pulls the stored f*(t) from global memory exactly as
+// nodes (62 x 22) and a slot array of kT2W x kT2H nodes (64 x 24, 48 KB of
+// FP32 populations): the tile grown by one node on every side.  Step 1 pulls the stored f*(t) from global memory exactly as
 // the single step does, collides every slot and keeps f*(t+1) of all slots in
 // shared memory; step 2 pulls f*(t+1) of the tile's nodes from shared memory
 // (their pull neighbours are the halo slots), collides again and stores
@@ -351,15 +370,19 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
 // The halo wraps at most once, which needs nx >= kT2W and ny >= kT2H
 // (step2_fits).  CHECK makes the second step the residual-check step of
 // k_step<..., CHECK> (snapshot compared with u^{t+1}, the second step's input
-// state) and is launched as a persistent grid; the plain variant has one
-// block per tile.
+// state); its snapshot loads are issued before the barrier between the steps.
 #ifndef LBM_T2_RPW
-#define LBM_T2_RPW 4
+#define LBM_T2_RPW 3
 #endif
 #ifndef LBM_MINB_T2
 #define LBM_MINB_T2 3
 #endif
+#ifndef LBM_T2_B
+#define LBM_T2_B 1
+#endif
 constexpr int kT2Rows = LBM_T2_RPW;             // slot rows per warp
+constexpr int kT2B = LBM_T2_B;                  // slot rows gathered together in step 1
+static_assert(kT2Rows % kT2B == 0, "rows per warp must be a multiple of the gather batch");
 constexpr int kT2W = 64;                        // slot columns (two per lane)
 constexpr int kT2H = 8 * kT2Rows;               // slot rows
 constexpr int kT2OX = kT2W - 2, kT2OY = kT2H - 2;
@@ -388,33 +411,56 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
     float gx[kT2Rows][2], gy[kT2Rows][2];
     // Step 1: f*(t+1) of every slot into shared memory.
 #pragma unroll
-    for (int k = 0; k < kT2Rows; ++k) {
-        const int r = warp + 8 * k;
-        int y = y0 + r;
-        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-        const int64_t r0 = (int64_t)y * nx;
-        const int64_t rm = (int64_t)wrap_dec(y, ny) * nx, rp = (int64_t)wrap_inc(y, ny) * nx;
-        float f[2][8];
+    for (int kb = 0; kb < kT2Rows; kb += kT2B) {
+        float f[kT2B][2][8];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            gather<S_F32>(a, r0, rm, rp, X[j], XM[j], XP[j], f[j], c.theta);
-            gx[k][j] = ldg(gxp + r0 + X[j]);
-            gy[k][j] = ldg(gyp + r0 + X[j]);
+        for (int b = 0; b < kT2B; ++b) {
+            const int k = kb + b;
+            int y = y0 + warp + 8 * k;
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            const int64_t r0 = (int64_t)y * nx;
+            const int64_t rm = (int64_t)wrap_dec(y, ny) * nx, rp = (int64_t)wrap_inc(y, ny) * nx;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                gather<S_F32>(a, r0, rm, rp, X[j], XM[j], XP[j], f[b][j], c.theta);
+                gx[k][j] = ldg(gxp + r0 + X[j]);
+                gy[k][j] = ldg(gyp + r0 + X[j]);
+            }
         }
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            float u, v, fs[8];
-            populations(collide<float, GEN>(moments(f[j]), gx[k][j], gy[k][j], c, u, v), fs);
-            float* s = sm + r * kT2W + lane + 32 * j;
+        for (int b = 0; b < kT2B; ++b) {
+            const int k = kb + b, r = warp + 8 * k;
 #pragma unroll
-            for (int p = 0; p < 8; ++p) s[p * PL] = fs[p];
+            for (int j = 0; j < 2; ++j) {
+                float u, v, fs[8];
+                populations(collide<float, GEN>(moments(f[b][j]), gx[k][j], gy[k][j], c, u, v), fs);
+                float* s = sm + r * kT2W + lane + 32 * j;
+#pragma unroll
+                for (int p = 0; p < 8; ++p) s[p * PL] = fs[p];
+            }
+        }
+    }
+    float* __restrict__ d = static_cast<float*>(a.dst);
+    float* __restrict__ snap = static_cast<float*>(a.snap);
+    const int64_t pl = a.plane, n = (int64_t)nx * ny;
+    float so[kT2Rows][2][2];
+    if (CHECK) {
+#pragma unroll
+        for (int k = 0; k < kT2Rows; ++k) {
+            const int r = warp + 8 * k, y = y0 + r;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int col = lane + 32 * j, x = x0 + col;
+                so[k][j][0] = so[k][j][1] = 0.0f;
+                if (r >= 1 && r <= kT2H - 2 && y < ny && col >= 1 && col <= kT2W - 2 && x < nx) {
+                    so[k][j][0] = snap[(int64_t)y * nx + x];
+                    so[k][j][1] = snap[n + (int64_t)y * nx + x];
+                }
+            }
         }
     }
     __syncthreads();
     // Step 2: the tile's nodes pull f*(t+1) from shared memory.
-    float* __restrict__ d = static_cast<float*>(a.dst);
-    float* __restrict__ snap = static_cast<float*>(a.snap);
-    const int64_t pl = a.plane, n = (int64_t)nx * ny;
 #pragma unroll
     for (int k = 0; k < kT2Rows; ++k) {
         const int r = warp + 8 * k;
@@ -426,11 +472,6 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             const int x = x0 + col;
             if (col < 1 || col > kT2W - 2 || x >= nx) continue;
             const int64_t idx = (int64_t)y * nx + x;
-            float so0 = 0.0f, so1 = 0.0f;
-            if (CHECK) {
-                so0 = snap[idx];
-                so1 = snap[n + idx];
-            }
             const float* s = sm + r * kT2W + col;
             float f[8];
             f[0] = s[0 * PL - 1];               // f_p(x) = f*_p(x - c_p)
@@ -448,7 +489,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             if (CHECK) {
                 snap[idx] = u;
                 snap[n + idx] = v;
-                const float du = u - so0, dv = v - so1;
+                const float du = u - so[k][j][0], dv = v - so[k][j][1];
                 acc[0] = fmaxf(acc[0], fmaxf(fabsf(du), fabsf(dv)));
                 acc[1] = fmaxf(acc[1], fmaxf(fabsf(u), fabsf(v)));
                 acc[2] += du * du + dv * dv;
@@ -591,8 +632,6 @@ struct Ops {
     // check_blocks: grid of the persistent CHECK launch (<= partials slots)
     static cudaError_t step(const StepParams& a, const Coef<T>& c, int V, bool gen, bool check,
                             int check_blocks, cudaStream_t st);
-    // resident blocks per SM of the CHECK kernel
-    static int check_occupancy(int V, bool gen);
     static cudaError_t fields(const StepParams& a, const Coef<double>& c, T theta, double* out,
                               cudaStream_t st);
     static cudaError_t export_pop(const StepParams& a, T theta, double* out, cudaStream_t st);
@@ -628,6 +667,9 @@ inline int64_t step_tiles(int nx, int ny, int V) {
     return (int64_t)((nx + 32 * V - 1) / (32 * V)) * ((ny + BY - 1) / BY);
 }
 
+// Grid cap of the residual-check launches: one FP64 partial set per block.
+constexpr int64_t kMaxCheckBlocks = int64_t(1) << 18;
+
 // Two-step launches (FP32): lattice large enough for a halo that wraps once.
 inline bool step2_fits(int nx, int ny) { return nx >= kT2W && ny >= kT2H; }
 
@@ -638,8 +680,6 @@ inline int64_t step2_tiles(int nx, int ny) {
 // Two fused steps of FP32 storage (k_step2); defined with the FP32 kernels.
 cudaError_t step2_f32(const StepParams& a, const Coef<float>& c, bool gen, bool check,
                       int check_blocks, cudaStream_t st);
-// resident blocks per SM of the two-step CHECK kernel
-int step2_check_occupancy(bool gen);
 
 inline dim3 step_grid(int nx, int ny, int V) {
     return dim3((unsigned)((nx + 32 * V - 1) / (32 * V)), (unsigned)((ny + BY - 1) / BY));

@@ -32,19 +32,6 @@ cudaError_t Ops<S>::step(const StepParams& a, const Coef<T>& c, int V, bool gen,
     return cudaGetLastError();
 }
 
-template <int S, int V>
-static int occ_v(bool gen) {
-    int b = 0;
-    if (gen) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S, V, true, true>, kThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S, V, false, true>, kThreads, 0);
-    return b > 0 ? b : 1;
-}
-
-template <int S>
-int Ops<S>::check_occupancy(int V, bool gen) {
-    return V == 1 ? occ_v<S, 1>(gen) : occ_v<S, max_vec<S>()>(gen);
-}
-
 template <int S>
 cudaError_t Ops<S>::fields(const StepParams& a, const Coef<double>& c, T theta, double* out,
                            cudaStream_t st) {

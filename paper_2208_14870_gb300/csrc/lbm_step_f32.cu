@@ -47,11 +47,4 @@ cudaError_t step2_f32(const StepParams& a, const Coef<float>& c, bool gen, bool 
     return cudaGetLastError();
 }
 
-int step2_check_occupancy(bool gen) {
-    if (t2_allow_smem() != cudaSuccess) return 1;
-    int b = 0;
-    if (gen) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step2<true, true>, kT2Threads, kT2Smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step2<false, true>, kT2Threads, kT2Smem);
-    return b > 0 ? b : 1;
-}
 }  // namespace lbm

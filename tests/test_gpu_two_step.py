@@ -31,9 +31,9 @@ def _pair(nx, ny, seed=1, **kw):
     return a, b, gx, gy, lam, mu
 
 
-# (64, 32) is the smallest lattice with two steps per launch; the others leave
-# ragged tiles in x and/or y (tile 62 x 30 nodes).
-@pytest.mark.parametrize("nx,ny", [(64, 32), (130, 70), (200, 97), (64, 300), (517, 33)])
+# (64, 24) is the smallest lattice with two steps per launch; the others leave
+# ragged tiles in x and/or y (tile 62 x 22 nodes).
+@pytest.mark.parametrize("nx,ny", [(64, 24), (130, 70), (200, 97), (64, 300), (517, 33)])
 @pytest.mark.parametrize("steps", [1, 2, 7])
 def test_two_step_launch_is_bit_identical(nx, ny, steps):
     a, b, *_ = _pair(nx, ny)
@@ -95,7 +95,7 @@ def test_two_step_matches_oracle():
 
 def test_steps_per_launch_availability():
     lam, mu = W.lame_2d(1.0, 0.3)
-    for nx, ny, dt, want in ((64, 32, "f32", 2), (63, 32, "f32", 1), (64, 31, "f32", 1),
+    for nx, ny, dt, want in ((64, 24, "f32", 2), (63, 32, "f32", 1), (64, 23, "f32", 1),
                              (256, 256, "f64", 1), (256, 256, "f16s", 1)):
         with Lattice(nx, ny, lam, mu, dt) as lat:
             assert lat.steps_per_launch == want, (nx, ny, dt)
