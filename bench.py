@@ -50,9 +50,9 @@ FORCE_SEED = 0x2208_14870
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32_x2": {"bytes_per_launch": (674.806016e6 + 494.653952e6) * 16, "kernel_hash": "088c5c35f9c159e2"},
-    "f32_x1": {"bytes_per_launch": (671.171072e6 + 486.934272e6) * 16, "kernel_hash": "234028f04f09fba8"},
-    "f16s_x1": {"bytes_per_launch": (536.991232e6 + 367.842816e6) * 16, "kernel_hash": "088c5c35f9c159e2"},
+    "f32_x2": {"bytes_per_launch": (674.817792e6 + 494.865920e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
+    "f32_x1": {"bytes_per_launch": (671.175936e6 + 486.552320e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
+    "f16s_x1": {"bytes_per_launch": (536.991232e6 + 368.358912e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
 }
 
 
@@ -282,8 +282,9 @@ def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, 
     lat.close()
     del out5
     per_iter = launches_per_iterate(args.iters, args.check_every, spl)
+    checks = args.iters // args.check_every      # each adds one residual-finish launch
     return {"total_ms": total_ms, "iter_ms": iter_ms, "steps": nsteps, "spl": spl,
-            "step_launches": nsteps * per_iter, "launches": nsteps * (per_iter + 1)}
+            "step_launches": nsteps * per_iter, "launches": nsteps * (per_iter + checks + 1)}
 
 
 def run_ours(args, ws, rank, local):
@@ -310,7 +311,7 @@ def run_ours(args, ws, rank, local):
     sampler = ClockSampler(local if ws > 1 else torch.cuda.current_device())
     barrier()
     sampler.start()
-    res = time_variant(args, args.dtype, gx_d, gy_d, torch, P, args.steps, args.warmup)
+    res = time_variant(args, args.dtype, gx_d, gy_d, torch, P, args.steps, args.warmup, spl=args.spl)
     barrier()
     clocks = sampler.stop()
     total_ms, lups = replica_aggregate(dist if ws > 1 else None, res["total_ms"],
@@ -541,6 +542,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--dtype", default="f32", choices=["f64", "f32", "f16s"])
     ap.add_argument("--nu", type=float, default=0.3)
+    ap.add_argument("--spl", type=int, default=None,
+                    help="steps per stream-collide launch of the main line (default: the library's choice)")
     ap.add_argument("--variants", nargs="*", default=["f16s", "f32x1"],
                     help="extra storage variants; a suffix xK fixes K steps per launch")
     ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")

@@ -57,7 +57,6 @@ struct lbm_ctx {
     void* force = nullptr;         // 2 planes of the storage force type
     void* snap = nullptr;          // 2*n of the snapshot type
     double* partials = nullptr;
-    unsigned int* counter = nullptr;
     double* result = nullptr;      // kRes doubles (device)
     unsigned long long* absmax = nullptr;
     unsigned int* bad = nullptr;
@@ -101,7 +100,7 @@ StepParams params(const lbm_ctx* c, int src) {
     a.hinv = c->hinv;
     a.snap = c->snap;
     a.partials = c->partials;
-    a.counter = c->counter;
+    a.counter = nullptr;   // check launches write partials; k_residual_finish combines them
     a.result = c->result;
     return a;
 }
@@ -124,6 +123,12 @@ Coef<T> coef(const lbm_rates& r) {
     return c;
 }
 
+// Residual of a check launch whose blocks wrote partials only.
+cudaError_t finish_residual_launch(lbm_ctx* c, int64_t grid) {
+    k_residual_finish<<<1, kFinishThreads, 0, c->stream>>>(c->partials, grid, c->result);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(lbm_ctx* c, bool check) {
     const StepParams a = params(c, c->cur);
     cudaError_t e;
@@ -132,6 +137,7 @@ cudaError_t launch_step(lbm_ctx* c, bool check) {
         case LBM_F32: e = Ops<S_F32>::step(a, coef<float>(c->rates), c->V, c->gen, check, (int)c->nblocks, c->stream); break;
         default: e = Ops<S_F16S>::step(a, coef<float>(c->rates), c->V, c->gen, check, (int)c->nblocks, c->stream); break;
     }
+    if (e == cudaSuccess && check) e = finish_residual_launch(c, c->nblocks);
     if (e == cudaSuccess) {
         c->cur ^= 1;
         c->step += 1;
@@ -144,6 +150,7 @@ cudaError_t launch_step(lbm_ctx* c, bool check) {
 cudaError_t launch_step2(lbm_ctx* c, bool check) {
     const StepParams a = params(c, c->cur);
     cudaError_t e = step2_f32(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks2, c->stream);
+    if (e == cudaSuccess && check) e = finish_residual_launch(c, c->nblocks2);
     if (e == cudaSuccess) {
         c->cur ^= 1;
         c->step += 2;
@@ -211,7 +218,6 @@ void free_all(lbm_ctx* c) {
     if (c->force) cudaFree(c->force);
     if (c->snap) cudaFree(c->snap);
     if (c->partials) cudaFree(c->partials);
-    if (c->counter) cudaFree(c->counter);
     if (c->result) cudaFree(c->result);
     if (c->absmax) cudaFree(c->absmax);
     if (c->bad) cudaFree(c->bad);
@@ -383,7 +389,6 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     if (e == cudaSuccess) e = alloc(&c->snap, snap_bytes);
     if (e == cudaSuccess) e = alloc((void**)&c->partials,
                                        sizeof(double) * kRes * std::max(c->nblocks, c->nblocks2));
-    if (e == cudaSuccess) e = alloc((void**)&c->counter, sizeof(unsigned int));
     if (e == cudaSuccess) e = alloc((void**)&c->result, sizeof(double) * kRes);
     if (e == cudaSuccess) e = alloc((void**)&c->absmax, sizeof(unsigned long long));
     if (e == cudaSuccess) e = alloc((void**)&c->bad, sizeof(unsigned int));
@@ -394,7 +399,6 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     if (e == cudaSuccess && dtype == LBM_F16S) e = cudaMemset(c->car[1], 0, cb);
     if (e == cudaSuccess) e = cudaMemset(c->force, 0, fb);
     if (e == cudaSuccess) e = cudaMemset(c->snap, 0, snap_bytes);
-    if (e == cudaSuccess) e = cudaMemset(c->counter, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         int code = cuda_fail(e, "lbm_create: device allocation");

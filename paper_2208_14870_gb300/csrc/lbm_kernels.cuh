@@ -194,6 +194,22 @@ __device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) 
     __syncthreads();
     const unsigned int nblocks = gridDim.x * gridDim.y;
     const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (a.counter == nullptr) {
+        // Partials only: a later k_residual_finish launch combines them, so
+        // the block ends here without a memory fence or a grid counter.
+        if (tid == 0) {
+            double w[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int i = 0; i < nwarps; ++i) {
+                w[0] = fmax(w[0], sh[0][i]);
+                w[1] = fmax(w[1], sh[1][i]);
+                w[2] += sh[2][i];
+                w[3] += sh[3][i];
+                w[4] = fmax(w[4], sh[4][i]);
+            }
+            for (int k = 0; k < kRes; ++k) a.partials[(int64_t)bid * kRes + k] = w[k];
+        }
+        return;
+    }
     if (tid == 0) {
         double w[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int i = 0; i < nwarps; ++i) {
@@ -408,7 +424,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
         XM[j] = wrap_dec(x, nx);
         XP[j] = wrap_inc(x, nx);
     }
-    float gx[kT2Rows][2], gy[kT2Rows][2];
+    float gx[kT2Rows][2], gy[kT2Rows][2];   // force of the thread's slots
     // Step 1: f*(t+1) of every slot into shared memory.
 #pragma unroll
     for (int kb = 0; kb < kT2Rows; kb += kT2B) {
@@ -430,13 +446,13 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
 #pragma unroll
         for (int b = 0; b < kT2B; ++b) {
             const int k = kb + b, r = warp + 8 * k;
+            float* s = sm + r * kT2W + lane;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 float u, v, fs[8];
                 populations(collide<float, GEN>(moments(f[b][j]), gx[k][j], gy[k][j], c, u, v), fs);
-                float* s = sm + r * kT2W + lane + 32 * j;
 #pragma unroll
-                for (int p = 0; p < 8; ++p) s[p * PL] = fs[p];
+                for (int p = 0; p < 8; ++p) s[p * PL + 32 * j] = fs[p];
             }
         }
     }
@@ -620,6 +636,12 @@ __global__ void k_absmax(const double* gx, const double* gy, int64_t n,
 
 // F16S: multiply every stored deviation by `factor` (a power of two).
 __global__ void k_rescale_half(__half* h, int64_t count, float factor);
+
+// Grid-level pass of the residual when the check launch wrote per-block
+// partials only (StepParams::counter == nullptr): one block combines the
+// nblocks partial sets (FP64) into result.
+__global__ void k_residual_finish(const double* partials, int64_t nblocks, double* result);
+constexpr int kFinishThreads = 1024;
 
 // Higher-order force correction with periodic central differences (FP64).
 __global__ void k_force_correct(const double* gx, const double* gy, double* ox, double* oy, int nx,
