@@ -43,6 +43,13 @@ FALLBACK_HBM_GBS = 6800.0
 # (FP32 two-step kernel): bytes per lattice update = this / steps per launch.
 BYTES_PER_LAUNCH_NODE = {"f64": 8 * 8 * 2 + 2 * 8, "f32": 8 * 4 * 2 + 2 * 4, "f16s": (8 * 2 + 2 * 4) * 2 + 2 * 4}
 FORCE_SEED = 0x2208_14870
+# FP64 storage runs its collision on the FP64 pipe: 48 FP64 instructions per
+# lattice update (ncu: 30 DADD, 11 DMUL, 7 DFMA per node), i.e. 55 flops.
+# Every FP64 instruction takes one slot of the pipe, whose nominal rate on
+# GB300 is 1.25 TFLOP/s counting an FMA as 2 flops, i.e. 625 G instructions/s.
+FP64_INSTR_PER_LUP = 48
+FP64_FLOPS_PER_LUP = 55
+FP64_PEAK_GINST = 625.0
 # DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype
 # and steps per launch,
 # with the hash of the kernel sources it was taken on (null once they change).
@@ -53,6 +60,7 @@ NCU_TRAFFIC = {
     "f32_x2": {"bytes_per_launch": (674.817792e6 + 494.865920e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
     "f32_x1": {"bytes_per_launch": (671.175936e6 + 486.552320e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
     "f16s_x1": {"bytes_per_launch": (536.991232e6 + 368.358912e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
+    "f16s_x2": {"bytes_per_launch": (539.921920e6 + 366.681088e6) * 16, "kernel_hash": "fde7484b5d564601"},
 }
 
 
@@ -243,9 +251,11 @@ def launches_per_iterate(iters, check_every, spl):
     return total + plain(left)
 
 
-def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, spl=None):
-    """Device-resident timing of `nsteps` benchmark steps; returns dict."""
+def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, spl=None, iters=None):
+    """Device-resident timing of `nsteps` benchmark steps of `iters`
+    pseudo-time steps each (default --iters); returns dict."""
     n = args.n
+    iters = args.iters if iters is None else iters
     lam, mu = W.lame_2d(1.0, args.nu)
     lat = P.Lattice(n, n, lam, mu, dtype)
     if spl is not None:
@@ -260,7 +270,7 @@ def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, 
         lat.reset()
         if ev_a is not None:
             ev_a.record(stream)
-        P.lbm_iterate_checked(lat.ctx, args.iters, args.check_every, None)
+        P.lbm_iterate_checked(lat.ctx, iters, args.check_every, None)
         if ev_b is not None:
             ev_b.record(stream)
         lat.fields_device(out5)
@@ -281,9 +291,9 @@ def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, 
     iter_ms = sum(a.elapsed_time(b) for a, b in evs)
     lat.close()
     del out5
-    per_iter = launches_per_iterate(args.iters, args.check_every, spl)
-    checks = args.iters // args.check_every      # each adds one residual-finish launch
-    return {"total_ms": total_ms, "iter_ms": iter_ms, "steps": nsteps, "spl": spl,
+    per_iter = launches_per_iterate(iters, args.check_every, spl)
+    checks = iters // args.check_every      # each adds one residual-finish launch
+    return {"total_ms": total_ms, "iter_ms": iter_ms, "steps": nsteps, "spl": spl, "iters": iters,
             "step_launches": nsteps * per_iter, "launches": nsteps * (per_iter + checks + 1)}
 
 
@@ -333,15 +343,27 @@ def run_ours(args, ws, rank, local):
             if name == args.dtype or dt not in BYTES_PER_LAUNCH_NODE:
                 continue
             r = time_variant(args, dt, gx_d, gy_d, torch, P, max(2, args.steps // 2), 2,
-                             spl=int(k) if k else None)
+                             spl=int(k) if k else None,
+                             iters=args.f64_iters if dt == "f64" else None)
             pl = r["iter_ms"] / 1e3 / r["step_launches"]
             b = BYTES_PER_LAUNCH_NODE[dt] * n * n
+            lups = float(n) * n * r["iters"] * r["steps"] / (r["total_ms"] / 1e3)
             variants[name] = {
-                "value": float(n) * n * args.iters * r["steps"] / (r["total_ms"] / 1e3) / 1e6,
-                "unit": "MLUPS", "ms_per_step": r["total_ms"] / r["steps"],
+                "value": lups / 1e6, "unit": "MLUPS", "ms_per_step": r["total_ms"] / r["steps"],
+                "iters_per_step": r["iters"],
                 "steps_per_launch": r["spl"], "kernel_us": pl * 1e6,
                 "achieved_gbs": b / pl / 1e9, "frac_of_measured_hbm": b / pl / 1e9 / peak,
                 "bytes_per_lup": BYTES_PER_LAUNCH_NODE[dt] / r["spl"]}
+            if dt == "f64":
+                # FP64 is bound by the FP64 pipe, not by HBM: FP64 instructions
+                # per second over the pipe's nominal instruction rate
+                gi = FP64_INSTR_PER_LUP * n * n / pl / 1e9
+                variants[name]["roofline"] = {
+                    "bound": "alu", "achieved": gi, "peak": FP64_PEAK_GINST, "unit": "G FP64 instr/s",
+                    "frac": gi / FP64_PEAK_GINST,
+                    "peak_kind": "nominal GB300 FP64 rate (1.25 TFLOP/s with FMA = 2 flops)",
+                    "fp64_instructions_per_lup": FP64_INSTR_PER_LUP, "flops_per_lup": FP64_FLOPS_PER_LUP,
+                    "achieved_tflops": FP64_FLOPS_PER_LUP * n * n / pl / 1e12}
 
     e2e = None
     if not args.no_e2e:
@@ -544,7 +566,9 @@ def main():
     ap.add_argument("--nu", type=float, default=0.3)
     ap.add_argument("--spl", type=int, default=None,
                     help="steps per stream-collide launch of the main line (default: the library's choice)")
-    ap.add_argument("--variants", nargs="*", default=["f16s", "f32x1"],
+    ap.add_argument("--f64-iters", type=int, default=100,
+                    help="pseudo-time steps per benchmark step of the FP64 variant")
+    ap.add_argument("--variants", nargs="*", default=["f16s", "f32x1", "f16sx1", "f64"],
                     help="extra storage variants; a suffix xK fixes K steps per launch")
     ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")
     ap.add_argument("--no-e2e", action="store_true")

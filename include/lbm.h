@@ -119,14 +119,17 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
 /* Pseudo-time steps per stream-collide launch: 1 or 2.  With 2, one launch
  * runs two consecutive steps of Algorithm 1 (Sec. 3.3, Eqs. collision and
  * streaming): the first step's post-collision state of a tile and its one-node
- * halo stays on chip, so the populations cross device memory once per two
- * steps.  The arithmetic per node is unchanged and the state after every
- * launch equals that of the same steps taken one per launch, bit for bit; a
- * residual check (lbm_iterate_checked, lbm_solve) falls on the second step of
- * a pair.  Available for LBM_F32 storage on lattices with nx >= 64 and
- * ny >= 24, where it is the default; other contexts run one step per launch.
- * Paper: the scheme advances one step at a time; the pairing is a schedule
- * of the same steps, not part of the method.
+ * halo stays on chip in FP32, so the populations cross device memory once per
+ * two steps.  A residual check (lbm_iterate_checked, lbm_solve) falls on the
+ * second step of a pair.  With LBM_F32 storage the arithmetic per node is
+ * unchanged and the state after every launch equals that of the same steps
+ * taken one per launch, bit for bit.  With LBM_F16S storage the intermediate
+ * state is not rounded to the FP16 storage format, so results differ from one
+ * step per launch by less than that format's rounding (and lie closer to the
+ * FP64 result).  Available for LBM_F32 and LBM_F16S storage on lattices with
+ * nx >= 64 and ny >= 24, where it is the default; other contexts run one step
+ * per launch.  Paper: the scheme advances one step at a time; the pairing is
+ * a schedule of the same steps, not part of the method.
  * Errors: LBM_ERR_ARG (k not 1 or 2, or k = 2 where it is not available). */
 int lbm_set_steps_per_launch(lbm_ctx *ctx, int k);
 int lbm_get_steps_per_launch(lbm_ctx *ctx, int *k);

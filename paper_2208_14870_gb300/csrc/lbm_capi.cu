@@ -145,11 +145,13 @@ cudaError_t launch_step(lbm_ctx* c, bool check) {
     return e;
 }
 
-// Two steps in one launch (FP32 storage, step2_fits); with check the second
-// step is the residual-check step.
+// Two steps in one launch (FP32 or FP16-shifted storage, step2_fits); with
+// check the second step is the residual-check step.
 cudaError_t launch_step2(lbm_ctx* c, bool check) {
     const StepParams a = params(c, c->cur);
-    cudaError_t e = step2_f32(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks2, c->stream);
+    cudaError_t e = c->dtype == LBM_F32
+                        ? step2_f32(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks2, c->stream)
+                        : step2_f16s(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks2, c->stream);
     if (e == cudaSuccess && check) e = finish_residual_launch(c, c->nblocks2);
     if (e == cudaSuccess) {
         c->cur ^= 1;
@@ -366,7 +368,7 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     }
     // residual-check grids: one block per tile up to kMaxCheckBlocks
     c->nblocks = std::min(step_tiles(nx, ny, c->V), kMaxCheckBlocks);
-    if (dtype == LBM_F32 && step2_fits(nx, ny)) {
+    if (dtype != LBM_F64 && step2_fits(nx, ny)) {
         c->spl = 2;
         c->nblocks2 = std::min(step2_tiles(nx, ny), kMaxCheckBlocks);
     }
@@ -428,9 +430,9 @@ int lbm_set_steps_per_launch(lbm_ctx* c, int k) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (k != 1 && k != 2) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: k must be 1 or 2");
-    if (k == 2 && !(c->dtype == LBM_F32 && step2_fits(c->nx, c->ny)))
-        return fail(LBM_ERR_ARG,
-                    "lbm_set_steps_per_launch: two steps per launch need FP32 storage, nx >= 64 and ny >= 24");
+    if (k == 2 && !(c->dtype != LBM_F64 && step2_fits(c->nx, c->ny)))
+        return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: two steps per launch need FP32 or FP16-shifted "
+                                 "storage, nx >= 64 and ny >= 24");
     if (k == 2 && c->nblocks2 == 0) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: not set up");
     c->spl = k;
     return LBM_OK;

@@ -367,7 +367,8 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
 }
 
 // ---------------------------------------------------------------------------
-// Two pseudo-time steps per launch, FP32 storage (temporal blocking).
+// Two pseudo-time steps per launch, FP32 or FP16-shifted storage (temporal
+// blocking).
 //
 // A block of 256 threads (8 warps) owns one output tile of kT2OX x kT2OY
 // nodes (62 x 22) and a slot array of kT2W x kT2H nodes (64 x 24, 48 KB of
@@ -377,11 +378,14 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
 // (their pull neighbours are the halo slots), collides again and stores
 // f*(t+2) of the tile.  The state crosses HBM once per two steps: per node and
 // launch 32 bytes read, 32 written and 8 of force read, i.e. 36 bytes per
-// lattice update instead of 72.  Thread (lane, warp) owns slot columns lane
-// and lane + 32 and slot rows warp + 8k in both steps, so the force it loaded
-// in step 1 serves step 2 from registers.  The per-node arithmetic is the
-// single step's (gather, collide, populations on the same FP32 values), so a
-// launch reproduces two single-step launches exactly.
+// lattice update instead of 72 (FP16-shifted: 28 instead of 56).  Thread
+// (lane, warp) owns slot columns lane and lane + 32 and slot rows warp + 8k in
+// both steps, so the force it loaded in step 1 serves step 2 from registers.
+// The per-node arithmetic is the single step's (gather, collide, populations),
+// so with FP32 storage a launch reproduces two single-step launches exactly.
+// With FP16-shifted storage the intermediate state f*(t+1) stays in FP32
+// (only the state written back is rounded to the storage format), so results
+// differ from one step per launch by less than the storage rounding.
 //
 // The halo wraps at most once, which needs nx >= kT2W and ny >= kT2H
 // (step2_fits).  CHECK makes the second step the residual-check step of
@@ -392,6 +396,9 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
 #endif
 #ifndef LBM_MINB_T2
 #define LBM_MINB_T2 3
+#endif
+#ifndef LBM_MINB_T2_F16S
+#define LBM_MINB_T2_F16S 4
 #endif
 #ifndef LBM_T2_B
 #define LBM_T2_B 1
@@ -406,7 +413,7 @@ constexpr int kT2Threads = 256;
 constexpr int kT2Smem = 8 * kT2H * kT2W * (int)sizeof(float);
 static_assert(kT2Threads == kThreads, "residual_reduce sizes its scratch by kThreads");
 
-template <bool GEN, bool CHECK>
+template <int S, bool GEN, bool CHECK>
 __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float>& c, float* sm,
                                            int tx, int ty, float acc[kRes]) {
     constexpr int PL = kT2H * kT2W;             // shared-memory plane
@@ -438,7 +445,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             const int64_t rm = (int64_t)wrap_dec(y, ny) * nx, rp = (int64_t)wrap_inc(y, ny) * nx;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                gather<S_F32>(a, r0, rm, rp, X[j], XM[j], XP[j], f[b][j], c.theta);
+                gather<S>(a, r0, rm, rp, X[j], XM[j], XP[j], f[b][j], c.theta);
                 gx[k][j] = ldg(gxp + r0 + X[j]);
                 gy[k][j] = ldg(gyp + r0 + X[j]);
             }
@@ -456,9 +463,8 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             }
         }
     }
-    float* __restrict__ d = static_cast<float*>(a.dst);
     float* __restrict__ snap = static_cast<float*>(a.snap);
-    const int64_t pl = a.plane, n = (int64_t)nx * ny;
+    const int64_t n = (int64_t)nx * ny;
     float so[kT2Rows][2][2];
     if (CHECK) {
 #pragma unroll
@@ -498,10 +504,8 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             f[5] = s[5 * PL - kT2W + 1];
             f[6] = s[6 * PL + kT2W + 1];
             f[7] = s[7 * PL + kT2W - 1];
-            float u, v, fs[8];
-            populations(collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), fs);
-#pragma unroll
-            for (int p = 0; p < 8; ++p) d[p * pl + idx] = fs[p];
+            float u, v;
+            scatter_local<S>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.theta);
             if (CHECK) {
                 snap[idx] = u;
                 snap[n + idx] = v;
@@ -516,8 +520,8 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
     }
 }
 
-template <bool GEN, bool CHECK>
-__global__ void __launch_bounds__(kT2Threads, CHECK ? 2 : LBM_MINB_T2)
+template <int S, bool GEN, bool CHECK>
+__global__ void __launch_bounds__(kT2Threads, CHECK ? 2 : (S == S_F16S ? LBM_MINB_T2_F16S : LBM_MINB_T2))
 k_step2(const StepParams a, const Coef<float> c) {
     extern __shared__ float t2_smem[];
     const int ntx = (a.nx + kT2OX - 1) / kT2OX;
@@ -525,7 +529,7 @@ k_step2(const StepParams a, const Coef<float> c) {
     float acc[kRes] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
-        step2_tile<GEN, CHECK>(a, c, t2_smem, tx, ty, acc);
+        step2_tile<S, GEN, CHECK>(a, c, t2_smem, tx, ty, acc);
         if (t + gridDim.x < ntiles) __syncthreads();   // slots are reused by the next tile
     }
     if (CHECK) residual_reduce<float>(a, acc);
@@ -692,16 +696,19 @@ inline int64_t step_tiles(int nx, int ny, int V) {
 // Grid cap of the residual-check launches: one FP64 partial set per block.
 constexpr int64_t kMaxCheckBlocks = int64_t(1) << 18;
 
-// Two-step launches (FP32): lattice large enough for a halo that wraps once.
+// Two-step launches: lattice large enough for a halo that wraps once.
 inline bool step2_fits(int nx, int ny) { return nx >= kT2W && ny >= kT2H; }
 
 inline int64_t step2_tiles(int nx, int ny) {
     return (int64_t)((nx + kT2OX - 1) / kT2OX) * ((ny + kT2OY - 1) / kT2OY);
 }
 
-// Two fused steps of FP32 storage (k_step2); defined with the FP32 kernels.
+// Two fused steps (k_step2) of FP32 or FP16-shifted storage; defined with
+// each storage type's kernels.
 cudaError_t step2_f32(const StepParams& a, const Coef<float>& c, bool gen, bool check,
                       int check_blocks, cudaStream_t st);
+cudaError_t step2_f16s(const StepParams& a, const Coef<float>& c, bool gen, bool check,
+                       int check_blocks, cudaStream_t st);
 
 inline dim3 step_grid(int nx, int ny, int V) {
     return dim3((unsigned)((nx + 32 * V - 1) / (32 * V)), (unsigned)((ny + BY - 1) / BY));

@@ -3,9 +3,52 @@
 // lbm_step_f16s.cu), which instantiates Ops<S> for its type.
 #pragma once
 
+#include <mutex>
+
 #include "lbm_kernels.cuh"
 
 namespace lbm {
+
+// The two-step kernels use more than 48 KB of dynamic shared memory, which
+// each device must allow once per kernel.
+template <int S>
+static cudaError_t t2_allow_smem() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    e = cudaFuncSetAttribute(k_step2<S, false, false>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, false, true>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, true, false>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, true, true>, at, kT2Smem);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+// Two fused steps: one block per tile (check: up to check_blocks blocks).
+template <int S>
+static cudaError_t launch_step2(const StepParams& a, const Coef<float>& c, bool gen, bool check,
+                                int check_blocks, cudaStream_t st) {
+    if (!step2_fits(a.nx, a.ny)) return cudaErrorInvalidValue;
+    cudaError_t e = t2_allow_smem<S>();
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = step2_tiles(a.nx, a.ny);
+    const unsigned int grid = (unsigned int)(check ? (tiles < check_blocks ? tiles : check_blocks) : tiles);
+    const dim3 block(kT2Threads);
+    if (gen) {
+        if (check) k_step2<S, true, true><<<grid, block, kT2Smem, st>>>(a, c);
+        else k_step2<S, true, false><<<grid, block, kT2Smem, st>>>(a, c);
+    } else {
+        if (check) k_step2<S, false, true><<<grid, block, kT2Smem, st>>>(a, c);
+        else k_step2<S, false, false><<<grid, block, kT2Smem, st>>>(a, c);
+    }
+    return cudaGetLastError();
+}
 
 
 template <int S, int V>

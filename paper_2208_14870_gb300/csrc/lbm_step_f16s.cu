@@ -3,4 +3,9 @@
 
 namespace lbm {
 template struct Ops<S_F16S>;
+
+cudaError_t step2_f16s(const StepParams& a, const Coef<float>& c, bool gen, bool check,
+                       int check_blocks, cudaStream_t st) {
+    return launch_step2<S_F16S>(a, c, gen, check, check_blocks, st);
+}
 }  // namespace lbm

@@ -1,7 +1,9 @@
-"""Two pseudo-time steps per launch (FP32 storage): the fused launch runs the
+"""Two pseudo-time steps per launch.  FP32 storage: the fused launch runs the
 same per-node arithmetic as two single-step launches, so the state must agree
 bit for bit with one step per launch, on ragged tiles, with general rates,
-across residual-check windows, and through lbm_solve."""
+across residual-check windows, and through lbm_solve.  FP16-shifted storage:
+the intermediate state stays in FP32, so the result must agree with one step
+per launch, and with the oracle, within the FP16S storage tolerance (2e-3)."""
 import numpy as np
 import pytest
 
@@ -96,7 +98,7 @@ def test_two_step_matches_oracle():
 def test_steps_per_launch_availability():
     lam, mu = W.lame_2d(1.0, 0.3)
     for nx, ny, dt, want in ((64, 24, "f32", 2), (63, 32, "f32", 1), (64, 23, "f32", 1),
-                             (256, 256, "f64", 1), (256, 256, "f16s", 1)):
+                             (256, 256, "f64", 1), (256, 256, "f16s", 2), (63, 64, "f16s", 1)):
         with Lattice(nx, ny, lam, mu, dt) as lat:
             assert lat.steps_per_launch == want, (nx, ny, dt)
             lat.steps_per_launch = 1
@@ -107,3 +109,43 @@ def test_steps_per_launch_availability():
                 lat.steps_per_launch = 2
             with pytest.raises(P.LBMError):
                 lat.steps_per_launch = 3
+
+
+def _rel(a, b):
+    return max(float(np.max(np.abs(a[i] - b[i]))) / float(np.max(np.abs(b[i]))) for i in range(a.shape[0]))
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 24), (130, 70), (517, 33)])
+def test_two_step_f16s_matches_single_step_and_oracle(nx, ny):
+    lam, mu = W.lame_2d(1.0, 0.3)
+    rates = oracle.relaxation_rates(lam, mu)
+    pw = W.random_force(nx, ny, 8, 4, seed=7)
+    gx, gy = W.random_force_grid(pw)
+    steps = 40
+    ref = oracle.fields(oracle.run(oracle.zero_state(nx, ny), gx, gy, rates, steps), gx, gy, rates)
+    out = {}
+    for spl in (1, 2):
+        with Lattice(nx, ny, lam, mu, "f16s") as lat:
+            lat.steps_per_launch = spl
+            lat.set_force(gx, gy)
+            lat.iterate_checked(steps, 10)
+            out[spl] = lat.fields()
+    e1, e2, d12 = _rel(out[1], ref), _rel(out[2], ref), _rel(out[2], out[1])
+    print("f16s one step/launch %.2e, two %.2e, between %.2e" % (e1, e2, d12))
+    assert e1 < 2e-3 and e2 < 2e-3 and d12 < 2e-3
+
+
+def test_two_step_f16s_conserves_mean_displacement():
+    """The carriers keep the first moments of the stored state exactly, with
+    or without the unrounded intermediate step."""
+    lam, mu = W.lame_2d(1.0, 0.3)
+    nx, ny = 128, 96
+    pw = W.random_force(nx, ny, 8, 4, seed=8)
+    gx, gy = W.random_force_grid(pw)
+    with Lattice(nx, ny, lam, mu, "f16s") as lat:
+        assert lat.steps_per_launch == 2
+        lat.set_force(gx, gy)
+        lat.iterate(2000)
+        u = lat.displacement()
+        scale = float(np.max(np.abs(u)))
+        assert abs(float(np.mean(u[0]))) < 1e-4 * scale and abs(float(np.mean(u[1]))) < 1e-4 * scale
