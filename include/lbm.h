@@ -126,11 +126,13 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
  * taken one per launch, bit for bit.  With LBM_F16S storage the intermediate
  * state is not rounded to the FP16 storage format, so results differ from one
  * step per launch by less than that format's rounding (and lie closer to the
- * FP64 result).  Available for LBM_F32 and LBM_F16S storage on lattices with
- * nx >= 64 and ny >= 24, where it is the default; other contexts run one step
- * per launch.  Paper: the scheme advances one step at a time; the pairing is
- * a schedule of the same steps, not part of the method.
- * Errors: LBM_ERR_ARG (k not 1 or 2, or k = 2 where it is not available). */
+ * FP64 result).  Available for LBM_F32 and LBM_F16S storage on any lattice;
+ * the default from nx >= 64 and ny >= 24 on (a smaller lattice fills the
+ * 64 x 24 on-chip tile more than once and is faster one step per launch).
+ * LBM_F64 storage always runs one step per launch.  Paper: the scheme advances
+ * one step at a time; the pairing is a schedule of the same steps, not part
+ * of the method.
+ * Errors: LBM_ERR_ARG (k not 1 or 2, or k = 2 with LBM_F64 storage). */
 int lbm_set_steps_per_launch(lbm_ctx *ctx, int k);
 int lbm_get_steps_per_launch(lbm_ctx *ctx, int *k);
 
@@ -247,11 +249,18 @@ const char *lbm_last_error(void);
  * residual check of Sec. 2.1 (reading of lbm_solve) is fused into the last step
  * of each chunk of check_every steps, per problem.  Converged problems drop
  * out of the tile list between chunks.  The chunk (accumulator reset, kernel,
- * read-back) is replayed from a CUDA graph.  The tile width (32, 64 or 128
- * columns) is chosen by an autotuner that times the first three chunks and
- * caches the choice per workload signature in $LBM_AUTOTUNE_CACHE (default
- * ~/.cache/lbm_gb300/autotune.txt; LBM_AUTOTUNE=0 ignores the cache).
+ * read-back) is replayed from a CUDA graph.  The tile shape is chosen by an
+ * autotuner that times the first chunks and caches the choice per workload
+ * signature in $LBM_AUTOTUNE_CACHE (default ~/.cache/lbm_gb300/autotune.txt;
+ * LBM_AUTOTUNE=0 ignores the cache): tiles 32, 64 or 128 columns wide (tile
+ * code 1, 2, 4: warps of 32 columns, one step per barrier) or, when
+ * check_every is even, LBM_TILE_TWO_STEP tiles (62 x 22 nodes, two steps per
+ * tile visit with the intermediate state on chip and one grid barrier per
+ * pair of steps; lbm_set_steps_per_launch describes the arithmetic).
  * ------------------------------------------------------------------------- */
+/* Tile code of two-step tiles in lbm_batch_report.tile_v and lbm_stats.tile_v. */
+#define LBM_TILE_TWO_STEP 3
+
 typedef struct lbm_problem {
     int nx, ny;                 /* lattice size, >= 1 */
     double lambda, mu;          /* Lame parameters, lattice units; theta = 1/3,
@@ -268,7 +277,7 @@ typedef struct lbm_result {
 } lbm_result;
 
 typedef struct lbm_batch_report {
-    int tile_v;                 /* tile width used, in warps of 32 columns */
+    int tile_v;                 /* tile code used: 1, 2, 4 (warps of 32 columns) or LBM_TILE_TWO_STEP */
     int blocks;                 /* persistent grid size */
     int64_t chunks;             /* chunk launches */
     int64_t lattice_updates;    /* sum over problems of nodes x steps */
@@ -318,7 +327,7 @@ typedef struct lbm_stats {
     int64_t chunks;
     size_t hbm_bytes;          /* device memory held by the arenas */
     int peak_running;          /* most problems resident at once */
-    int tile_v;                /* tile width in warps of 32 columns */
+    int tile_v;                /* tile code: 1, 2, 4 (warps of 32 columns) or LBM_TILE_TWO_STEP */
     int failed;                /* LBM_OK, or the error that stopped the worker */
 } lbm_stats;
 

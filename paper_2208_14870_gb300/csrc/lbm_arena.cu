@@ -100,6 +100,90 @@ __global__ void __launch_bounds__(kThreads, 2) k_arena_chunk(const BatchArgs A) 
     }
 }
 
+// One tile of two steps (k_step2's tile) of problem P; s counts step pairs.
+template <int S, bool CHECK>
+__device__ __forceinline__ void arena_tile2(const BatchArgs& A, const BatchProb& P, int tile, int s,
+                                            float* sm, float acc[kRes]) {
+    StepParams a{};
+    const int64_t n = (int64_t)P.nx * P.ny;
+    a.nx = P.nx;
+    a.ny = P.ny;
+    a.plane = n;
+    const int src = (P.parity + s) & 1;
+    a.src = (src ? A.pop1 : A.pop0) + P.pop_off;
+    a.dst = (src ? A.pop0 : A.pop1) + P.pop_off;
+    if (S == S_F16S) {
+        a.csrc = reinterpret_cast<const float*>((src ? A.car1 : A.car0) + P.car_off);
+        a.cdst = reinterpret_cast<float*>((src ? A.car0 : A.car1) + P.car_off);
+        a.hscale = P.hscale;
+        a.hinv = P.hinv;
+    }
+    float* fsb = reinterpret_cast<float*>(A.fs + P.fs_off);
+    a.gx = fsb;
+    a.gy = fsb + n;
+    a.snap = fsb + 2 * n;
+    Coef<float> c{};
+    c.a11 = P.a11;
+    c.as = P.as;
+    c.ad = P.ad;
+    c.theta = P.theta;
+    const int ntx = (P.nx + kT2OX - 1) / kT2OX;
+    const int ty = tile / ntx, tx = tile - ty * ntx;
+    step2_tile<S, false, CHECK>(a, c, sm, tx, ty, acc);
+}
+
+// The chunk with two steps per tile visit and one grid barrier per pair of
+// steps (nsteps even); the residual check rides on the second step of the
+// chunk's last pair.
+template <int S>
+__global__ void __launch_bounds__(kT2Threads, 2) k_arena_chunk2(const BatchArgs A) {
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ float t2_smem[];
+    __shared__ float red[kRes][kThreads / 32];
+    const int ntiles = *A.ntiles;
+    const int npairs = A.nsteps / 2;
+    for (int s = 0; s < npairs; ++s) {
+        const bool last = (s == npairs - 1);
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const uint2 tl = A.tiles[t];
+            const BatchProb P = A.probs[tl.x];
+            const bool check = last && P.check;  // uniform over the block
+            float acc[kRes] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            if (!check) {
+                arena_tile2<S, false>(A, P, (int)tl.y, s, t2_smem, acc);
+            } else {
+                arena_tile2<S, true>(A, P, (int)tl.y, s, t2_smem, acc);
+                tile_to_problem(acc, A.acc + (int64_t)tl.x * kRes, red);
+            }
+            __syncthreads();   // the slots are reused by the block's next tile
+        }
+        if (s + 1 < npairs) grid.sync();
+    }
+}
+
+template <int S>
+static cudaError_t t2_arena_allow_smem() {
+    return cudaFuncSetAttribute(k_arena_chunk2<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2Smem);
+}
+
+template <int S>
+static cudaError_t launch_two_step(const BatchArgs& a, int grid, cudaStream_t st) {
+    if (a.nsteps % 2) return cudaErrorInvalidValue;
+    cudaError_t e = t2_arena_allow_smem<S>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kT2Threads);
+    cfg.dynamicSmemBytes = kT2Smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_arena_chunk2<S>, a);
+}
+
 template <int S, int V>
 static cudaError_t launch_v(const BatchArgs& a, int grid, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
@@ -116,6 +200,8 @@ static cudaError_t launch_v(const BatchArgs& a, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_arena_chunk(int dtype, int V, const BatchArgs& a, int grid, cudaStream_t st) {
+    if (V == kTileTwoStep)
+        return dtype == S_F16S ? launch_two_step<S_F16S>(a, grid, st) : launch_two_step<S_F32>(a, grid, st);
     if (dtype == S_F16S) {
         switch (V) {
             case 1: return launch_v<S_F16S, 1>(a, grid, st);
@@ -139,7 +225,16 @@ static int occ() {
     return b;
 }
 
+template <int S>
+static int occ2() {
+    if (t2_arena_allow_smem<S>() != cudaSuccess) return 0;
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_arena_chunk2<S>, kT2Threads, kT2Smem);
+    return b;
+}
+
 int arena_occupancy(int dtype, int V) {
+    if (V == kTileTwoStep) return dtype == S_F16S ? occ2<S_F16S>() : occ2<S_F32>();
     if (dtype == S_F16S) return V == 1 ? occ<S_F16S, 1>() : V == 2 ? occ<S_F16S, 2>() : occ<S_F16S, 4>();
     return V == 1 ? occ<S_F32, 1>() : V == 2 ? occ<S_F32, 2>() : occ<S_F32, 4>();
 }

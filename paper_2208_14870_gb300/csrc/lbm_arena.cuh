@@ -100,10 +100,19 @@ private:
     int64_t cap_ = 0;
 };
 
+// Tile code of two-step tiles: the 62 x 22-node tiles of k_step2, two steps
+// per tile visit and one grid barrier per pair of steps (chunk length even).
+constexpr int kTileTwoStep = 3;
+
+// Number of tiles of an nx x ny problem for tile code V.
+inline int64_t arena_tiles(int nx, int ny, int V) {
+    return V == kTileTwoStep ? step2_tiles(nx, ny) : step_tiles(nx, ny, V);
+}
+
 // Launch one chunk: nsteps steps of every listed tile (all of storage type
 // dtype: S_F32 or S_F16S), residual check fused into the last step.  Tile
-// width 32*V, V in {1, 2, 4}.  Cooperative launch: grid must not exceed
-// arena_occupancy(dtype, V) x SM count.
+// code V: width 32*V for V in {1, 2, 4}, or kTileTwoStep.  Cooperative
+// launch: grid must not exceed arena_occupancy(dtype, V) x SM count.
 cudaError_t launch_arena_chunk(int dtype, int V, const BatchArgs& a, int grid, cudaStream_t st);
 // Resident blocks per SM of the chunk kernel.
 int arena_occupancy(int dtype, int V);

@@ -84,33 +84,36 @@ extern "C" int lbm_batch_solve(int count, const lbm_problem* probs, int dtype, d
             else if (s < 0) rc = s;
             slot[i] = s;
         }
-        // Autotuner: the first three chunks (which do the same work: no
-        // problem can retire before the second check) run with tile widths
-        // 32, 64 and 128 and the fastest per tile-step is kept and cached.
+        // Autotuner: the first chunks run with tile widths 32, 64 and 128
+        // and, for an even chunk length, with two-step tiles; the fastest per
+        // active node and chunk is kept and cached.
         const std::string key = signature(count, probs, dtype, check_every);
+        const bool even = check_every % 2 == 0;
         int V = rc == LBM_OK ? autotune_lookup(key) : 0;
-        if (const char* force_v = std::getenv("LBM_BATCH_TILE_V")) {  // fixed width, no tuning
+        if (V == kTileTwoStep && !even) V = 0;
+        if (const char* force_v = std::getenv("LBM_BATCH_TILE_V")) {  // fixed shape, no tuning
             const int fv = std::atoi(force_v);
-            if (fv == 1 || fv == 2 || fv == 4) V = fv;
+            if (fv == 1 || fv == 2 || fv == 4 || (fv == kTileTwoStep && even)) V = fv;
         }
-        const int cand[3] = {1, 2, 4};
+        const int cand[4] = {1, 2, 4, kTileTwoStep};
+        const int ncand = even ? 4 : 3;
         double best = 1e300;
-        int tuning = V == 0 ? 0 : 3;
+        int tuning = V == 0 ? 0 : ncand;
         while (rc == LBM_OK && eng.running() > 0) {
-            const int v = tuning < 3 ? cand[tuning] : V;
+            const int v = tuning < ncand ? cand[tuning] : V;
             const int64_t active_nodes = eng.running_nodes();
             float ms = 0.0f;
             rc = eng.run_chunk(v, &ms, &err);
             if (rc) break;
             ++chunks;
             dev_ms += ms;
-            if (tuning < 3) {
+            if (tuning < ncand) {
                 const double per = ms / (double)std::max<int64_t>(active_nodes, 1);
                 if (per < best) {
                     best = per;
                     V = v;
                 }
-                if (++tuning == 3) autotune_store(key, V);
+                if (++tuning == ncand) autotune_store(key, V);
             }
         }
         chosen_V = V;

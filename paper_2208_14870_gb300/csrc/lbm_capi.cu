@@ -145,8 +145,8 @@ cudaError_t launch_step(lbm_ctx* c, bool check) {
     return e;
 }
 
-// Two steps in one launch (FP32 or FP16-shifted storage, step2_fits); with
-// check the second step is the residual-check step.
+// Two steps in one launch (FP32 or FP16-shifted storage); with check the
+// second step is the residual-check step.
 cudaError_t launch_step2(lbm_ctx* c, bool check) {
     const StepParams a = params(c, c->cur);
     cudaError_t e = c->dtype == LBM_F32
@@ -368,9 +368,9 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     }
     // residual-check grids: one block per tile up to kMaxCheckBlocks
     c->nblocks = std::min(step_tiles(nx, ny, c->V), kMaxCheckBlocks);
-    if (dtype != LBM_F64 && step2_fits(nx, ny)) {
-        c->spl = 2;
+    if (dtype != LBM_F64) {
         c->nblocks2 = std::min(step2_tiles(nx, ny), kMaxCheckBlocks);
+        if (step2_fits(nx, ny)) c->spl = 2;
     }
 
     const size_t pb = pop_elem_bytes(dtype) * 8 * c->plane;
@@ -430,10 +430,8 @@ int lbm_set_steps_per_launch(lbm_ctx* c, int k) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (k != 1 && k != 2) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: k must be 1 or 2");
-    if (k == 2 && !(c->dtype != LBM_F64 && step2_fits(c->nx, c->ny)))
-        return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: two steps per launch need FP32 or FP16-shifted "
-                                 "storage, nx >= 64 and ny >= 24");
-    if (k == 2 && c->nblocks2 == 0) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: not set up");
+    if (k == 2 && c->dtype == LBM_F64)
+        return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: two steps per launch need FP32 or FP16-shifted storage");
     c->spl = k;
     return LBM_OK;
 }

@@ -11,6 +11,8 @@
 #include "../../include/lbm.h"
 #include "lbm_engine.cuh"
 
+static_assert(lbm::kTileTwoStep == LBM_TILE_TWO_STEP, "tile code of two-step tiles");
+
 namespace lbm {
 
 namespace {
@@ -192,7 +194,7 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
 int64_t ArenaEngine::running_tiles(int V) const {
     int64_t t = 0;
     for (const auto& p : probs_)
-        if (p.state == P_RUNNING) t += step_tiles(p.nx, p.ny, V);
+        if (p.state == P_RUNNING) t += arena_tiles(p.nx, p.ny, V);
     return t;
 }
 
@@ -241,7 +243,7 @@ int ArenaEngine::upload_tiles(int V, std::string* err) {
     for (int s = 0; s < (int)probs_.size(); ++s) {
         const HostProb& p = probs_[s];
         if (p.state != P_RUNNING) continue;
-        const int64_t m = step_tiles(p.nx, p.ny, V);
+        const int64_t m = arena_tiles(p.nx, p.ny, V);
         for (int64_t i = 0; i < m; ++i) h_tiles_[t++] = make_uint2((unsigned)s, (unsigned)i);
     }
     static thread_local int nt_host;
@@ -291,8 +293,8 @@ int ArenaEngine::ensure_graph(int V, std::string* err) {
 }
 
 int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
-    if (V != 1 && V != 2 && V != 4) {
-        if (err) *err = "arena: tile width must be 1, 2 or 4 warps of 32";
+    if (V != 1 && V != 2 && V != 4 && !(V == kTileTwoStep && k_ % 2 == 0)) {
+        if (err) *err = "arena: tile code must be 1, 2 or 4 warps of 32, or two-step tiles with an even chunk";
         return LBM_ERR_ARG;
     }
     if (device_ms) *device_ms = 0.0f;
@@ -362,7 +364,8 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
         if (p.state != P_RUNNING) continue;
         p.steps += k_;
         p.lups += p.n * k_;
-        if (k_ & 1) {
+        // the buffers swap once per launch-level step: k steps, or k/2 pairs
+        if ((V == kTileTwoStep ? (k_ / 2) : k_) & 1) {
             p.parity ^= 1;
             desc_dirty_ = true;
         }

@@ -387,8 +387,10 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
 // (only the state written back is rounded to the storage format), so results
 // differ from one step per launch by less than the storage rounding.
 //
-// The halo wraps at most once, which needs nx >= kT2W and ny >= kT2H
-// (step2_fits).  CHECK makes the second step the residual-check step of
+// Any lattice size works (slot coordinates wrap periodically; a lattice
+// smaller than the slot array appears in it more than once); the
+// single-lattice path uses it from nx >= kT2W and ny >= kT2H (step2_fits),
+// the batched arena for every problem.  CHECK makes the second step the residual-check step of
 // k_step<..., CHECK> (snapshot compared with u^{t+1}, the second step's input
 // state); its snapshot loads are issued before the barrier between the steps.
 #ifndef LBM_T2_RPW
@@ -413,6 +415,14 @@ constexpr int kT2Threads = 256;
 constexpr int kT2Smem = 8 * kT2H * kT2W * (int)sizeof(float);
 static_assert(kT2Threads == kThreads, "residual_reduce sizes its scratch by kThreads");
 
+// Periodic image in [0, n) of a slot coordinate v >= -1 (one conditional
+// wrap when n is at least the slot span, a remainder on smaller lattices).
+__device__ __forceinline__ int wrap_slot(int v, int n) {
+    if (v < 0) v += n;
+    if (v >= n) v = v < 2 * n ? v - n : v % n;
+    return v;
+}
+
 template <int S, bool GEN, bool CHECK>
 __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float>& c, float* sm,
                                            int tx, int ty, float acc[kRes]) {
@@ -425,8 +435,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
     int X[2], XM[2], XP[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        int x = x0 + lane + 32 * j;
-        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+        const int x = wrap_slot(x0 + lane + 32 * j, nx);
         X[j] = x;
         XM[j] = wrap_dec(x, nx);
         XP[j] = wrap_inc(x, nx);
@@ -439,8 +448,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
 #pragma unroll
         for (int b = 0; b < kT2B; ++b) {
             const int k = kb + b;
-            int y = y0 + warp + 8 * k;
-            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            const int y = wrap_slot(y0 + warp + 8 * k, ny);
             const int64_t r0 = (int64_t)y * nx;
             const int64_t rm = (int64_t)wrap_dec(y, ny) * nx, rp = (int64_t)wrap_inc(y, ny) * nx;
 #pragma unroll
@@ -696,7 +704,8 @@ inline int64_t step_tiles(int nx, int ny, int V) {
 // Grid cap of the residual-check launches: one FP64 partial set per block.
 constexpr int64_t kMaxCheckBlocks = int64_t(1) << 18;
 
-// Two-step launches: lattice large enough for a halo that wraps once.
+// Two-step launches of a single lattice: from one full slot array up (smaller
+// lattices would mostly compute duplicate slots).
 inline bool step2_fits(int nx, int ny) { return nx >= kT2W && ny >= kT2H; }
 
 inline int64_t step2_tiles(int nx, int ny) {

@@ -34,7 +34,6 @@ static cudaError_t t2_allow_smem() {
 template <int S>
 static cudaError_t launch_step2(const StepParams& a, const Coef<float>& c, bool gen, bool check,
                                 int check_blocks, cudaStream_t st) {
-    if (!step2_fits(a.nx, a.ny)) return cudaErrorInvalidValue;
     cudaError_t e = t2_allow_smem<S>();
     if (e != cudaSuccess) return e;
     const int64_t tiles = step2_tiles(a.nx, a.ny);

@@ -57,7 +57,7 @@ def test_batch_matches_single_lattice_and_fixed_point(dtype, tol, k, tol_fix):
     probs = make_problems(SIZES)
     results, report = P.batch_solve([p[:6] for p in probs], dtype=dtype, tol=tol,
                                     check_every=k, max_iters=2_000_000)
-    assert report["tile_v"] in (1, 2, 4) and report["chunks"] >= 3
+    assert report["tile_v"] in (1, 2, 4, P.LBM_TILE_TWO_STEP) and report["chunks"] >= 4
     for (nx, ny, lam, mu, gx, gy, pw), r in zip(probs, results):
         assert r["status"] == P.LBM_OK, (nx, ny, r)
         rates = oracle.relaxation_rates(lam, mu)
@@ -111,3 +111,26 @@ def test_batch_rejects_bad_arguments():
         P.batch_solve(probs, dtype="f64")
     with pytest.raises(P.LBMError):
         P.batch_solve(probs, check_every=1)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16s"])
+def test_batch_two_step_tiles_match_one_step_tiles(dtype, monkeypatch):
+    """Two-step arena tiles (two steps per tile visit, one grid barrier per
+    pair) against 128-column one-step tiles: FP32 bit for bit, with the same
+    stopping step; FP16S within its storage tolerance.  The problems include
+    lattices smaller than the 64 x 24 on-chip tile."""
+    probs = make_problems(SIZES, seed=11)
+    out = {}
+    for v in (4, P.LBM_TILE_TWO_STEP):
+        monkeypatch.setenv("LBM_BATCH_TILE_V", str(v))
+        results, report = P.batch_solve([p[:6] for p in probs], dtype=dtype, tol=1e-6, check_every=100,
+                                        max_iters=400_000)
+        assert report["tile_v"] == v
+        out[v] = results
+    for a, b in zip(out[4], out[P.LBM_TILE_TWO_STEP]):
+        assert a["status"] == b["status"] == P.LBM_OK
+        if dtype == "f32":
+            assert a["iters"] == b["iters"]
+            assert np.array_equal(a["fields"], b["fields"])
+        else:
+            assert rel_per_field(b["fields"], a["fields"]) < 2e-3

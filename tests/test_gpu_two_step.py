@@ -96,19 +96,40 @@ def test_two_step_matches_oracle():
 
 
 def test_steps_per_launch_availability():
+    """Default: two steps from 64 x 24 on for FP32 and FP16S; any FP32/FP16S
+    lattice may choose two; FP64 always one."""
     lam, mu = W.lame_2d(1.0, 0.3)
     for nx, ny, dt, want in ((64, 24, "f32", 2), (63, 32, "f32", 1), (64, 23, "f32", 1),
                              (256, 256, "f64", 1), (256, 256, "f16s", 2), (63, 64, "f16s", 1)):
         with Lattice(nx, ny, lam, mu, dt) as lat:
             assert lat.steps_per_launch == want, (nx, ny, dt)
             lat.steps_per_launch = 1
-            if want == 1:
+            if dt == "f64":
                 with pytest.raises(P.LBMError):
                     lat.steps_per_launch = 2
             else:
                 lat.steps_per_launch = 2
+                assert lat.steps_per_launch == 2
             with pytest.raises(P.LBMError):
                 lat.steps_per_launch = 3
+
+
+# Lattices smaller than the 64 x 24 slot array appear in it more than once
+# (periodic images); the result must still equal single steps bit for bit.
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 3), (5, 5), (33, 17), (63, 23), (7, 130), (130, 7)])
+def test_two_step_small_lattice_is_bit_identical(nx, ny):
+    lam, mu = W.lame_2d(1.0, 0.3)
+    pw = W.random_force(nx, ny, 4, 3, seed=9)
+    gx, gy = W.random_force_grid(pw)
+    out = []
+    for spl in (1, 2):
+        with Lattice(nx, ny, lam, mu, "f32") as lat:
+            lat.steps_per_launch = spl
+            lat.set_force(gx, gy)
+            r = lat.iterate_checked(9, 3)
+            out.append((lat.populations(), r))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1][0] == out[1][1][0]
 
 
 def _rel(a, b):
