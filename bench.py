@@ -459,6 +459,62 @@ def plain_solve(P, p, tol, k, dtype="f32"):
     return st, it
 
 
+def run_sweep(args, P):
+    """Convergence and stability sweep (the sinusoidal manufactured field at
+    wavenumbers 1 and 4, E = 1, nu in {0, 0.2, 0.3, 0.4, 0.45}, N from 32 up):
+    per storage type the relative error of u and sigma against the analytic
+    field after ln(1/eps) / r steps (r = min(2 a^2 (mu + K), 0.05), a = 2 pi
+    k / N: the decay rate of the forced mode, capped where the lattice's other
+    modes decay slower), the observed order between successive N,
+    and the device rate.  FP64 stops at --sweep-f64-max (its FP64-pipe rate
+    makes N = 2048 minutes long)."""
+    import torch
+    eps = {"f64": 1e-13, "f32": 1e-8, "f16s": 1e-6}
+    ns = [n for n in (32, 64, 128, 256, 512, 1024, 2048) if n <= args.sweep_max_n]
+    rows = []
+    stream = torch.cuda.current_stream()
+    for dt in ("f64", "f32", "f16s"):
+        for k in (1, 4):
+            for nu in (0.0, 0.2, 0.3, 0.4, 0.45):
+                prev = None
+                for n in ns:
+                    if dt == "f64" and n > args.sweep_f64_max:
+                        continue
+                    lam, mu = W.lame_2d(1.0, nu)
+                    man = W.sinusoid(n, k, lam, mu)
+                    gx, gy = man.force()
+                    # the forced mode decays at r = 2 a^2 (mu + K) per step while
+                    # that is small; the non-hydrodynamic modes at ~0.05 or faster
+                    a = 2.0 * np.pi * k / n
+                    r = min(2.0 * a * a * (2.0 * mu + lam), 0.05)
+                    steps = int(np.ceil(np.log(1.0 / eps[dt]) / r))
+                    with P.Lattice(n, n, lam, mu, dt) as lat:
+                        lat.set_stream(stream.cuda_stream)
+                        lat.set_force(gx, gy)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        lat.iterate(steps)
+                        e1.record(stream)
+                        got = lat.fields()
+                        ms = e0.elapsed_time(e1)
+                    ex = man.exact()
+                    eu = max(float(np.max(np.abs(got[i] - ex[i]))) / float(np.max(np.abs(ex[i]))) for i in (0, 1))
+                    es = max(float(np.max(np.abs(got[i] - ex[i]))) / float(np.max(np.abs(ex[i]))) for i in (2, 3, 4))
+                    row = {"dtype": dt, "k": k, "nu": nu, "n": n, "steps": steps, "err_u": eu, "err_sigma": es,
+                           "glups": float(n) * n * steps / (ms / 1e3) / 1e9,
+                           "order_u": None if prev is None else float(np.log2(prev / eu))}
+                    prev = eu
+                    rows.append(row)
+                    print("sweep %-4s k=%d nu=%.2f N=%5d steps=%8d err_u=%.3e err_sigma=%.3e order=%s" % (
+                        dt, k, nu, n, steps, eu, es, "-" if row["order_u"] is None else "%.2f" % row["order_u"]),
+                        file=sys.stderr, flush=True)
+    return {"workload": "convergence and stability sweep: sinusoidal manufactured field, wavenumbers 1 and 4, "
+                        "nu in {0, 0.2, 0.3, 0.4, 0.45}, N = 32..%d (FP64 to %d), error vs the analytic field "
+                        "after ln(1/eps)/r steps" % (ns[-1], args.sweep_f64_max),
+            "eps": eps, "rows": rows}
+
+
 def run_batched(args, P):
     """Config-4 stream (2048 problems, sides log-uniform in [32, 1024], nu in
     [0, 0.45], 8 random force modes, FP32, tol 1e-8): the problems whose longer
@@ -585,8 +641,10 @@ def main():
     ap.add_argument("--served-cap", type=int, default=256)
     ap.add_argument("--served-max", type=int, default=300)
     ap.add_argument("--served-rate", type=float, default=300.0)
-    ap.add_argument("--only", choices=["batched", "served"], default=None,
-                    help="run one secondary workload alone and print its JSON (profiling)")
+    ap.add_argument("--sweep-max-n", type=int, default=2048)
+    ap.add_argument("--sweep-f64-max", type=int, default=512)
+    ap.add_argument("--only", choices=["batched", "served", "sweep"], default=None,
+                    help="run one secondary workload alone and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -595,7 +653,7 @@ def main():
         import torch
         torch.cuda.set_device(local)
         import paper_2208_14870_gb300 as P
-        out = run_batched(args, P) if args.only == "batched" else run_served(args, P)
+        out = {"batched": run_batched, "served": run_served, "sweep": run_sweep}[args.only](args, P)
         print(json.dumps({"only": args.only, **out}), flush=True)
         return
     if args.impl == "reference":

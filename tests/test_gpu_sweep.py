@@ -1,0 +1,91 @@
+"""Convergence and stability sweep (the manufactured sinusoidal field of the
+sweep workload: u_x = sin(2 pi k x~) cos(2 pi k y~), u_y = cos(2 pi k x~)
+sin(2 pi k y~), E = 1), through the C ABI on the GPU:
+
+  * every storage type against the FP64 oracle's exact discrete steady state
+    (Sec. 4 operator, per Fourier mode) for N in {32, 64, 128}, every nu of
+    the sweep and wavenumbers 1 and 4, after ln(1/eps) / r steps with r the
+    decay rate 2 a^2 (mu + K) of the forced mode (a = 2 pi k / N), which
+    leaves a relative transient below eps;
+  * FP64 and FP32 against the analytic continuous field: the error falls
+    with second order in N (Sec. 6.3.1).
+
+Tolerances against the fixed point: FP64 1e-10 (steady state), FP32 2e-5,
+FP16S 2e-3 relative to the field's maximum (displacement and stress)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.fourier as F
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2208_14870_gb300 import Lattice  # noqa: E402
+
+NUS = (0.0, 0.2, 0.3, 0.4, 0.45)
+TOL = {"f64": 1e-10, "f32": 2e-5, "f16s": 2e-3}
+EPS = {"f64": 1e-13, "f32": 1e-8, "f16s": 1e-6}
+
+
+def steps_for(n, k, lam, mu, eps):
+    """Steps after which the transient of the forced wave vectors (a, +-a),
+    a = 2 pi k / n, is below eps: every eigenmode there decays at least like
+    rho^t, rho the spectral radius of the amplification matrix L(a, +-a)
+    (Sec. 4); a factor 1.5 covers the non-normal start of the decay."""
+    rates = oracle.relaxation_rates(lam, mu)
+    a = 2.0 * math.pi * k / n
+    rho = max(float(np.max(np.abs(np.linalg.eigvals(F.amplification_matrix(rates, a, s * a)))))
+              for s in (1.0, -1.0))
+    return int(math.ceil(1.5 * math.log(1.0 / eps) / -math.log(rho)))
+
+
+def rel(a, b):
+    return max(float(np.max(np.abs(a[i] - b[i]))) / float(np.max(np.abs(b[i]))) for i in range(a.shape[0]))
+
+
+def run(n, k, nu, dtype):
+    lam, mu = W.lame_2d(1.0, nu)
+    man = W.sinusoid(n, k, lam, mu)
+    gx, gy = man.force()
+    steps = steps_for(n, k, lam, mu, EPS[dtype])
+    with Lattice(n, n, lam, mu, dtype) as lat:
+        lat.set_force(gx, gy)
+        lat.iterate(steps)
+        return lat.fields(), man, lam, mu, steps
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+@pytest.mark.parametrize("k", [1, 4])
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_sweep_matches_oracle_fixed_point(n, k, dtype):
+    worst = 0.0
+    for nu in NUS:
+        got, man, lam, mu, steps = run(n, k, nu, dtype)
+        rates = oracle.relaxation_rates(lam, mu)
+        ks, _, fl = F.steady_state_modes(n, n, man.force_modes(), rates)
+        X, Y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
+        fixed = np.stack([F.evaluate_modes(ks, fl[:, c], X, Y) for c in range(5)])
+        e = max(rel(got[:2], fixed[:2]), rel(got[2:], fixed[2:]))
+        worst = max(worst, e)
+        assert e < TOL[dtype], (n, k, nu, dtype, e, steps)
+    print("%s N=%d k=%d: worst error vs oracle fixed point %.2e" % (dtype, n, k, worst))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("nu", [0.0, 0.3, 0.45])
+def test_sweep_second_order_convergence(dtype, nu):
+    errs = []
+    for n in (32, 64, 128):
+        got, man, *_ = run(n, 1, nu, dtype)
+        errs.append(rel(got[:2], man.exact()[:2]))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    print("%s nu=%.2f: displacement errors %s, orders %s" % (dtype, nu, errs, orders))
+    for p in orders:
+        assert 1.8 < p < 2.2, (errs, orders)
