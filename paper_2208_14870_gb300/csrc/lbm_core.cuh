@@ -71,49 +71,71 @@ __device__ __forceinline__ Mom<T> moments(const T f[8]) {
 // GEN = false is the standard case w_12 = w_21 = w_22 = 1 (Sec. 3.3.2),
 // where m*_12 = theta u, m*_21 = theta v, m*_22 = 0.
 // u, v receive the displacement mbar_10, mbar_01 (Table 2).
+//
+// Returned in the form the back-transform consumes ("quarter form"): m*_10
+// and m*_01 as they are, the moments of order two and higher (11, s, d, 12,
+// 21, 22) divided by 4.  The 1/4 rides on the relaxation coefficients, and
+// since 4 is a power of two, (c/4) * m rounds to exactly (c * m)/4: the
+// stored populations are the same bits as without it, at six fewer
+// multiplications per node.
 template <typename T, bool GEN>
 __device__ __forceinline__ Mom<T> collide(const Mom<T>& m, T gx, T gy, const Coef<T>& c,
                                           T& u, T& v) {
+    const T q = T(0.25);
     Mom<T> s;
     u = m.m10 + T(0.5) * gx;
     v = m.m01 + T(0.5) * gy;
     s.m10 = m.m10 + gx;
     s.m01 = m.m01 + gy;
-    s.m11 = rmul(c.a11, m.m11);
-    s.ms = rmul(c.as, m.ms);
-    s.md = rmul(c.ad, m.md);
+    s.m11 = rmul(q * c.a11, m.m11);
+    s.ms = rmul(q * c.as, m.ms);
+    s.md = rmul(q * c.ad, m.md);
     if (GEN) {
-        s.m12 = fmad(c.w12t, u, rmul(c.a12, m.m12));
-        s.m21 = fmad(c.w21t, v, rmul(c.a21, m.m21));
-        s.m22 = rmul(c.a22, m.m22);
+        s.m12 = fmad(q * c.w12t, u, rmul(q * c.a12, m.m12));
+        s.m21 = fmad(q * c.w21t, v, rmul(q * c.a21, m.m21));
+        s.m22 = rmul(q * c.a22, m.m22);
     } else {
-        s.m12 = rmul(c.theta, u);
-        s.m21 = rmul(c.theta, v);
+        s.m12 = rmul(q * c.theta, u);
+        s.m21 = rmul(q * c.theta, v);
         s.m22 = T(0);
     }
     return s;
 }
 
-// Back-transformation f = M^-1 m (Eq. moments_post solved in closed form):
-//   A = m10 - m12, B = m01 - m21, P = (ms - 2 m22 + md)/2, Q = (ms - 2 m22 - md)/2
-//   f1 = (P + A)/2, f3 = (P - A)/2, f2 = (Q + B)/2, f4 = (Q - B)/2
-//   f5 = (m22 + m11 + m12 + m21)/4, f6 = (m22 - m11 - m12 + m21)/4,
-//   f7 = (m22 + m11 - m12 - m21)/4, f8 = (m22 - m11 + m12 - m21)/4.
+// Raw moments in quarter form (for states that did not come from collide).
+template <typename T>
+__device__ __forceinline__ Mom<T> quarter(Mom<T> m) {
+    const T q = T(0.25);
+    m.m11 = q * m.m11;
+    m.ms = q * m.ms;
+    m.md = q * m.md;
+    m.m12 = q * m.m12;
+    m.m21 = q * m.m21;
+    m.m22 = q * m.m22;
+    return m;
+}
+
+// Back-transformation f = M^-1 m (Eq. moments_post solved in closed form),
+// from the quarter form (m11 ... m22 below are the moments divided by 4):
+//   A = m10 - 4 m12, B = m01 - 4 m21, P = ms - 2 m22 + md, Q = ms - 2 m22 - md
+//   f1 = P + A/2, f3 = P - A/2, f2 = Q + B/2, f4 = Q - B/2
+//   f5 = m22 + m11 + m12 + m21, f6 = m22 - m11 - m12 + m21,
+//   f7 = m22 + m11 - m12 - m21, f8 = m22 - m11 + m12 - m21.
 template <typename T>
 __device__ __forceinline__ void populations(const Mom<T>& s, T f[8]) {
-    const T A = s.m10 - s.m12, B = s.m01 - s.m21;
-    const T t = s.ms - T(2) * s.m22;
-    const T P = T(0.25) * (t + s.md), Q = T(0.25) * (t - s.md);
-    f[0] = P + T(0.5) * A;
-    f[2] = P - T(0.5) * A;
-    f[1] = Q + T(0.5) * B;
-    f[3] = Q - T(0.5) * B;
+    const T A = fmad(T(-4), s.m12, s.m10), B = fmad(T(-4), s.m21, s.m01);
+    const T t = fmad(T(-2), s.m22, s.ms);
+    const T P = t + s.md, Q = t - s.md;
+    f[0] = fmad(T(0.5), A, P);
+    f[2] = fmad(T(-0.5), A, P);
+    f[1] = fmad(T(0.5), B, Q);
+    f[3] = fmad(T(-0.5), B, Q);
     const T h1 = s.m22 + s.m11, h2 = s.m22 - s.m11;
     const T h3 = s.m12 + s.m21, h4 = s.m21 - s.m12;
-    f[4] = T(0.25) * (h1 + h3);
-    f[6] = T(0.25) * (h1 - h3);
-    f[5] = T(0.25) * (h2 + h4);
-    f[7] = T(0.25) * (h2 - h4);
+    f[4] = h1 + h3;
+    f[6] = h1 - h3;
+    f[5] = h2 + h4;
+    f[7] = h2 - h4;
 }
 
 // Shifted FP16 storage.  The equilibrium-type part of a post-collision state
@@ -124,13 +146,15 @@ __device__ __forceinline__ void populations(const Mom<T>& s, T f[8]) {
 //   E8 = k5 (c10 - c01)                                     (k5 = theta/4)
 // The stored deviation is N = f* - E = M^-1 (0, 0, m*_11, m*_s, m*_d,
 // m*_12 - theta m*_10, m*_21 - theta m*_01, m*_22), which is O(eps) of f*.
+// (Quarter form in and out: the m*_12 - theta m*_10 terms are divided by 4.)
 template <typename T>
 __device__ __forceinline__ Mom<T> deviation_moments(const Mom<T>& s, T theta) {
+    const T qt = T(-0.25) * theta;
     Mom<T> n = s;
     n.m10 = T(0);
     n.m01 = T(0);
-    n.m12 = fmad(-theta, s.m10, s.m12);
-    n.m21 = fmad(-theta, s.m01, s.m21);
+    n.m12 = fmad(qt, s.m10, s.m12);
+    n.m21 = fmad(qt, s.m01, s.m21);
     return n;
 }
 

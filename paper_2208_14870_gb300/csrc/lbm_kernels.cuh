@@ -621,7 +621,7 @@ k_import(const StepParams a, typename StoreT<S>::T theta, const double* in) {
     if constexpr (S == S_F16S) {
         const Mom<T> s = moments(fs);
         T nf[8];
-        populations(deviation_moments(s, theta), nf);
+        populations(deviation_moments(quarter(s), theta), nf);
         (void)d;
         store_f16s(a, idx, nf, s.m10, s.m01);
     } else {
