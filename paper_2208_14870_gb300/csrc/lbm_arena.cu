@@ -33,9 +33,10 @@ __device__ __forceinline__ void arena_tile(const BatchArgs& A, const BatchProb& 
     a.gy = fsb + n;
     a.snap = fsb + 2 * n;
     Coef<float> c{};
-    c.a11 = P.a11;
-    c.as = P.as;
-    c.ad = P.ad;
+    c.q11 = P.q11;
+    c.qs = P.qs;
+    c.qd = P.qd;
+    c.qtheta = P.qtheta;
     c.theta = P.theta;
     const int ntx = (P.nx + 32 * V - 1) / (32 * V);
     const int ty = tile / ntx, tx = tile - ty * ntx;
@@ -123,13 +124,14 @@ __device__ __forceinline__ void arena_tile2(const BatchArgs& A, const BatchProb&
     a.gy = fsb + n;
     a.snap = fsb + 2 * n;
     Coef<float> c{};
-    c.a11 = P.a11;
-    c.as = P.as;
-    c.ad = P.ad;
+    c.q11 = P.q11;
+    c.qs = P.qs;
+    c.qd = P.qd;
+    c.qtheta = P.qtheta;
     c.theta = P.theta;
     const int ntx = (P.nx + kT2OX - 1) / kT2OX;
     const int ty = tile / ntx, tx = tile - ty * ntx;
-    step2_tile<S, false, CHECK>(a, c, sm, tx, ty, acc);
+    step2_tile<S, false, CHECK, true>(a, c, sm, tx, ty, acc);
 }
 
 // The chunk with two steps per tile visit and one grid barrier per pair of

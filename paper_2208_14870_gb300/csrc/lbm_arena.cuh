@@ -33,7 +33,7 @@ struct BatchProb {
     int64_t car_off;   // bytes into each carrier buffer (F16S)
     int64_t fs_off;    // bytes into the force/snapshot buffer
     int nx, ny, check, dtype, parity;   // check: this chunk's last step checks
-    float a11, as, ad, theta, hscale, hinv;
+    float q11, qs, qd, qtheta, theta, hscale, hinv;   // rates in the quarter form of collide
 };
 
 struct BatchArgs {

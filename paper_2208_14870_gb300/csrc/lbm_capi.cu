@@ -108,14 +108,16 @@ StepParams params(const lbm_ctx* c, int src) {
 template <typename T>
 Coef<T> coef(const lbm_rates& r) {
     Coef<T> c;
-    c.a11 = T(1.0 - r.w11);
-    c.as = T(1.0 - r.ws);
-    c.ad = T(1.0 - r.wd);
-    c.w12t = T(r.w12 * r.theta);
-    c.a12 = T(1.0 - r.w12);
-    c.w21t = T(r.w21 * r.theta);
-    c.a21 = T(1.0 - r.w21);
-    c.a22 = T(1.0 - r.w22);
+    // quarter form (exact scaling by 1/4 before the rounding to T)
+    c.q11 = T(0.25 * (1.0 - r.w11));
+    c.qs = T(0.25 * (1.0 - r.ws));
+    c.qd = T(0.25 * (1.0 - r.wd));
+    c.qw12t = T(0.25 * (r.w12 * r.theta));
+    c.q12 = T(0.25 * (1.0 - r.w12));
+    c.qw21t = T(0.25 * (r.w21 * r.theta));
+    c.q21 = T(0.25 * (1.0 - r.w21));
+    c.q22 = T(0.25 * (1.0 - r.w22));
+    c.qtheta = T(0.25 * r.theta);
     c.theta = T(r.theta);
     c.b11 = T(1.0 - 0.5 * r.w11);
     c.bs = T(1.0 - 0.5 * r.ws);

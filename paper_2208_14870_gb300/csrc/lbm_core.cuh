@@ -31,14 +31,17 @@ struct Mom {
     T m10, m01, m11, ms, md, m12, m21, m22;
 };
 
-// Per-lattice constants of the collision in compute precision.
-//   a11 = 1 - w11, as = 1 - ws, ad = 1 - wd          (Eq. collision, m^eq = 0)
-//   w12t = w12 * theta, a12 = 1 - w12, ...            (m^eq_12 = theta mbar_10)
+// Per-lattice constants of the collision in compute precision, in the
+// quarter form collide returns (every factor of a second-order moment
+// divided by 4; see collide):
+//   q11 = (1 - w11)/4, qs = (1 - ws)/4, qd = (1 - wd)/4     (Eq. collision, m^eq = 0)
+//   qw12t = w12 theta / 4, q12 = (1 - w12)/4, ...          (m^eq_12 = theta mbar_10)
+//   qtheta = theta / 4; theta itself for the FP16-shifted store
 template <typename T>
 struct Coef {
-    T a11, as, ad;
-    T w12t, a12, w21t, a21, a22;
-    T theta;
+    T q11, qs, qd;
+    T qw12t, q12, qw21t, q21, q22;
+    T qtheta, theta;
     T b11, bs, bd;   // 1 - w/2 (bared moments, Eq. compute_bared)
 };
 
@@ -74,29 +77,28 @@ __device__ __forceinline__ Mom<T> moments(const T f[8]) {
 //
 // Returned in the form the back-transform consumes ("quarter form"): m*_10
 // and m*_01 as they are, the moments of order two and higher (11, s, d, 12,
-// 21, 22) divided by 4.  The 1/4 rides on the relaxation coefficients, and
-// since 4 is a power of two, (c/4) * m rounds to exactly (c * m)/4: the
-// stored populations are the same bits as without it, at six fewer
-// multiplications per node.
+// 21, 22) divided by 4.  The 1/4 rides on the coefficients (Coef), and since
+// 4 is a power of two, (c/4) * m rounds to exactly (c * m)/4: the stored
+// populations are the same bits as without it, at six fewer multiplications
+// per node.
 template <typename T, bool GEN>
 __device__ __forceinline__ Mom<T> collide(const Mom<T>& m, T gx, T gy, const Coef<T>& c,
                                           T& u, T& v) {
-    const T q = T(0.25);
     Mom<T> s;
     u = m.m10 + T(0.5) * gx;
     v = m.m01 + T(0.5) * gy;
     s.m10 = m.m10 + gx;
     s.m01 = m.m01 + gy;
-    s.m11 = rmul(q * c.a11, m.m11);
-    s.ms = rmul(q * c.as, m.ms);
-    s.md = rmul(q * c.ad, m.md);
+    s.m11 = rmul(c.q11, m.m11);
+    s.ms = rmul(c.qs, m.ms);
+    s.md = rmul(c.qd, m.md);
     if (GEN) {
-        s.m12 = fmad(q * c.w12t, u, rmul(q * c.a12, m.m12));
-        s.m21 = fmad(q * c.w21t, v, rmul(q * c.a21, m.m21));
-        s.m22 = rmul(q * c.a22, m.m22);
+        s.m12 = fmad(c.qw12t, u, rmul(c.q12, m.m12));
+        s.m21 = fmad(c.qw21t, v, rmul(c.q21, m.m21));
+        s.m22 = rmul(c.q22, m.m22);
     } else {
-        s.m12 = rmul(q * c.theta, u);
-        s.m21 = rmul(q * c.theta, v);
+        s.m12 = rmul(c.qtheta, u);
+        s.m21 = rmul(c.qtheta, v);
         s.m22 = T(0);
     }
     return s;
@@ -146,15 +148,15 @@ __device__ __forceinline__ void populations(const Mom<T>& s, T f[8]) {
 //   E8 = k5 (c10 - c01)                                     (k5 = theta/4)
 // The stored deviation is N = f* - E = M^-1 (0, 0, m*_11, m*_s, m*_d,
 // m*_12 - theta m*_10, m*_21 - theta m*_01, m*_22), which is O(eps) of f*.
-// (Quarter form in and out: the m*_12 - theta m*_10 terms are divided by 4.)
+// (Quarter form in and out: the m*_12 - theta m*_10 terms are divided by 4;
+// qtheta = theta / 4.)
 template <typename T>
-__device__ __forceinline__ Mom<T> deviation_moments(const Mom<T>& s, T theta) {
-    const T qt = T(-0.25) * theta;
+__device__ __forceinline__ Mom<T> deviation_moments(const Mom<T>& s, T qtheta) {
     Mom<T> n = s;
     n.m10 = T(0);
     n.m01 = T(0);
-    n.m12 = fmad(qt, s.m10, s.m12);
-    n.m21 = fmad(qt, s.m01, s.m21);
+    n.m12 = fmad(-qtheta, s.m10, s.m12);
+    n.m21 = fmad(-qtheta, s.m01, s.m21);
     return n;
 }
 

@@ -176,9 +176,10 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
     // Table 1 / Eq. relaxation_rate with theta = 1/3, w_12 = w_21 = w_22 = 1
     const double theta = 1.0 / 3.0, K = lambda + mu;
     p.theta = (float)theta;
-    p.a11 = (float)(1.0 - 1.0 / (mu / theta + 0.5));
-    p.as = (float)(1.0 - 1.0 / (2.0 * K / (1.0 + theta) + 0.5));
-    p.ad = (float)(1.0 - 1.0 / (2.0 * mu / (1.0 - theta) + 0.5));
+    p.qtheta = (float)(0.25 * theta);   // quarter form of collide
+    p.q11 = (float)(0.25 * (1.0 - 1.0 / (mu / theta + 0.5)));
+    p.qs = (float)(0.25 * (1.0 - 1.0 / (2.0 * K / (1.0 + theta) + 0.5)));
+    p.qd = (float)(0.25 * (1.0 - 1.0 / (2.0 * mu / (1.0 - theta) + 0.5)));
     p.hexp = dtype_ == S_F16S ? f16s_exponent(gmax, nx, ny) : 0;
     p.tol = tol;
     p.max_iters = max_iters;
@@ -324,9 +325,10 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
             b.check = p.check_now ? 1 : 0;
             b.dtype = dtype_;
             b.parity = p.parity;
-            b.a11 = p.a11;
-            b.as = p.as;
-            b.ad = p.ad;
+            b.q11 = p.q11;
+            b.qs = p.qs;
+            b.qd = p.qd;
+            b.qtheta = p.qtheta;
             b.theta = p.theta;
             b.hscale = std::ldexp(1.0f, p.hexp);
             b.hinv = std::ldexp(1.0f, -p.hexp);

@@ -24,7 +24,7 @@ struct HostProb {
     int64_t pop_bytes = 0, car_bytes = 0, fs_bytes = 0;
     int parity = 0;
     int hexp = 0;
-    float a11 = 0, as = 0, ad = 0, theta = 0;
+    float q11 = 0, qs = 0, qd = 0, qtheta = 0, theta = 0;   // rates in the quarter form of collide
     int64_t steps = 0;
     int64_t max_iters = 0;
     double tol = 0.0;

@@ -147,20 +147,21 @@ __device__ __forceinline__ void store_f16s(const StepParams& a, int64_t idx, con
 }
 
 // Store the post-collision state of node idx.
+// (s in the quarter form of collide; qtheta = theta / 4.)
 template <int S>
 __device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
                                               const Mom<typename StoreT<S>::T>& s,
-                                              typename StoreT<S>::T theta) {
+                                              typename StoreT<S>::T qtheta) {
     using T = typename StoreT<S>::T;
     using P = typename StoreT<S>::P;
     P* d = static_cast<P*>(a.dst);
     const int64_t pl = a.plane;
     T f[8];
     if constexpr (S == S_F16S) {
-        populations(deviation_moments(s, theta), f);
+        populations(deviation_moments(s, qtheta), f);
         store_f16s(a, idx, f, s.m10, s.m01);
     } else {
-        (void)theta;
+        (void)qtheta;
         populations(s, f);
 #pragma unroll
         for (int p = 0; p < 8; ++p) d[p * pl + idx] = P(f[p]);
@@ -336,7 +337,7 @@ __device__ __forceinline__ void step_tile(const StepParams& a,
             const int64_t idx = r0 + x;
             T u, v;
             const Mom<T> s = collide<T, GEN>(moments(f[j]), gx[j], gy[j], c, u, v);
-            scatter_local<S>(a, idx, s, c.theta);
+            scatter_local<S>(a, idx, s, c.qtheta);
             if (CHECK) {
                 const U uu = U(u), vv = U(v);
                 snap[idx] = uu;
@@ -387,12 +388,14 @@ k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
 // (only the state written back is rounded to the storage format), so results
 // differ from one step per launch by less than the storage rounding.
 //
-// Any lattice size works (slot coordinates wrap periodically; a lattice
-// smaller than the slot array appears in it more than once); the
-// single-lattice path uses it from nx >= kT2W and ny >= kT2H (step2_fits),
-// the batched arena for every problem.  CHECK makes the second step the residual-check step of
-// k_step<..., CHECK> (snapshot compared with u^{t+1}, the second step's input
-// state); its snapshot loads are issued before the barrier between the steps.
+// Any lattice size works: slot coordinates wrap periodically, and a lattice
+// smaller than the slot array appears in it more than once (ANY = true, the
+// general wrap; the batched arena uses it for every problem).  A lattice of
+// at least kT2W x kT2H (step2_fits) takes the ANY = false kernel, whose wrap
+// is one conditional subtraction.  CHECK makes the second step the
+// residual-check step of k_step<..., CHECK> (snapshot compared with u^{t+1},
+// the second step's input state); its snapshot loads are issued before the
+// barrier between the steps.
 #ifndef LBM_T2_RPW
 #define LBM_T2_RPW 3
 #endif
@@ -415,15 +418,19 @@ constexpr int kT2Threads = 256;
 constexpr int kT2Smem = 8 * kT2H * kT2W * (int)sizeof(float);
 static_assert(kT2Threads == kThreads, "residual_reduce sizes its scratch by kThreads");
 
-// Periodic image in [0, n) of a slot coordinate v >= -1 (one conditional
-// wrap when n is at least the slot span, a remainder on smaller lattices).
+// Periodic image in [0, n) of a slot coordinate v >= -1.  ANY = false
+// needs n at least the slot span (one conditional subtraction); ANY = true
+// serves any n (a lattice smaller than the slot array appears in it more
+// than once).  The two are separate kernels because the general form costs
+// the large-lattice kernel 4-6 % even where it never takes the long path.
+template <bool ANY>
 __device__ __forceinline__ int wrap_slot(int v, int n) {
     if (v < 0) v += n;
-    if (v >= n) v = v < 2 * n ? v - n : v % n;
+    if (v >= n) v = (!ANY || v < 2 * n) ? v - n : v % n;
     return v;
 }
 
-template <int S, bool GEN, bool CHECK>
+template <int S, bool GEN, bool CHECK, bool ANY>
 __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float>& c, float* sm,
                                            int tx, int ty, float acc[kRes]) {
     constexpr int PL = kT2H * kT2W;             // shared-memory plane
@@ -435,7 +442,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
     int X[2], XM[2], XP[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        const int x = wrap_slot(x0 + lane + 32 * j, nx);
+        const int x = wrap_slot<ANY>(x0 + lane + 32 * j, nx);
         X[j] = x;
         XM[j] = wrap_dec(x, nx);
         XP[j] = wrap_inc(x, nx);
@@ -448,7 +455,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
 #pragma unroll
         for (int b = 0; b < kT2B; ++b) {
             const int k = kb + b;
-            const int y = wrap_slot(y0 + warp + 8 * k, ny);
+            const int y = wrap_slot<ANY>(y0 + warp + 8 * k, ny);
             const int64_t r0 = (int64_t)y * nx;
             const int64_t rm = (int64_t)wrap_dec(y, ny) * nx, rp = (int64_t)wrap_inc(y, ny) * nx;
 #pragma unroll
@@ -513,7 +520,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             f[6] = s[6 * PL + kT2W + 1];
             f[7] = s[7 * PL + kT2W - 1];
             float u, v;
-            scatter_local<S>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.theta);
+            scatter_local<S>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
             if (CHECK) {
                 snap[idx] = u;
                 snap[n + idx] = v;
@@ -528,7 +535,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
     }
 }
 
-template <int S, bool GEN, bool CHECK>
+template <int S, bool GEN, bool CHECK, bool ANY>
 __global__ void __launch_bounds__(kT2Threads, CHECK ? 2 : (S == S_F16S ? LBM_MINB_T2_F16S : LBM_MINB_T2))
 k_step2(const StepParams a, const Coef<float> c) {
     extern __shared__ float t2_smem[];
@@ -537,7 +544,7 @@ k_step2(const StepParams a, const Coef<float> c) {
     float acc[kRes] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
-        step2_tile<S, GEN, CHECK>(a, c, t2_smem, tx, ty, acc);
+        step2_tile<S, GEN, CHECK, ANY>(a, c, t2_smem, tx, ty, acc);
         if (t + gridDim.x < ntiles) __syncthreads();   // slots are reused by the next tile
     }
     if (CHECK) residual_reduce<float>(a, acc);
@@ -621,7 +628,7 @@ k_import(const StepParams a, typename StoreT<S>::T theta, const double* in) {
     if constexpr (S == S_F16S) {
         const Mom<T> s = moments(fs);
         T nf[8];
-        populations(deviation_moments(quarter(s), theta), nf);
+        populations(deviation_moments(quarter(s), T(0.25) * theta), nf);
         (void)d;
         store_f16s(a, idx, nf, s.m10, s.m01);
     } else {

@@ -69,14 +69,15 @@ Coef<T> standard_coef(double lambda, double mu) {
     const double ws = 1.0 / (2.0 * K / (1.0 + theta) + 0.5);
     const double wd = 1.0 / (2.0 * mu / (1.0 - theta) + 0.5);
     Coef<T> c{};
-    c.a11 = T(1.0 - w11);
-    c.as = T(1.0 - ws);
-    c.ad = T(1.0 - wd);
-    c.w12t = T(theta);
-    c.a12 = T(0.0);
-    c.w21t = T(theta);
-    c.a21 = T(0.0);
-    c.a22 = T(0.0);
+    c.q11 = T(0.25 * (1.0 - w11));   // quarter form of collide
+    c.qs = T(0.25 * (1.0 - ws));
+    c.qd = T(0.25 * (1.0 - wd));
+    c.qw12t = T(0.25 * theta);
+    c.q12 = T(0.0);
+    c.qw21t = T(0.25 * theta);
+    c.q21 = T(0.0);
+    c.q22 = T(0.0);
+    c.qtheta = T(0.25 * theta);
     c.theta = T(theta);
     c.b11 = T(1.0 - 0.5 * w11);
     c.bs = T(1.0 - 0.5 * ws);

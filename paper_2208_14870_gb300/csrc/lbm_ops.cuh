@@ -22,10 +22,14 @@ static cudaError_t t2_allow_smem() {
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev]) return cudaSuccess;
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    e = cudaFuncSetAttribute(k_step2<S, false, false>, at, kT2Smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, false, true>, at, kT2Smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, true, false>, at, kT2Smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, true, true>, at, kT2Smem);
+    e = cudaFuncSetAttribute(k_step2<S, false, false, false>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, false, true, false>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, true, false, false>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, true, true, false>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, false, false, true>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, false, true, true>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, true, false, true>, at, kT2Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2<S, true, true, true>, at, kT2Smem);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -39,12 +43,20 @@ static cudaError_t launch_step2(const StepParams& a, const Coef<float>& c, bool 
     const int64_t tiles = step2_tiles(a.nx, a.ny);
     const unsigned int grid = (unsigned int)(check ? (tiles < check_blocks ? tiles : check_blocks) : tiles);
     const dim3 block(kT2Threads);
-    if (gen) {
-        if (check) k_step2<S, true, true><<<grid, block, kT2Smem, st>>>(a, c);
-        else k_step2<S, true, false><<<grid, block, kT2Smem, st>>>(a, c);
+    if (!step2_fits(a.nx, a.ny)) {   // lattice smaller than the slot array
+        if (gen) {
+            if (check) k_step2<S, true, true, true><<<grid, block, kT2Smem, st>>>(a, c);
+            else k_step2<S, true, false, true><<<grid, block, kT2Smem, st>>>(a, c);
+        } else {
+            if (check) k_step2<S, false, true, true><<<grid, block, kT2Smem, st>>>(a, c);
+            else k_step2<S, false, false, true><<<grid, block, kT2Smem, st>>>(a, c);
+        }
+    } else if (gen) {
+        if (check) k_step2<S, true, true, false><<<grid, block, kT2Smem, st>>>(a, c);
+        else k_step2<S, true, false, false><<<grid, block, kT2Smem, st>>>(a, c);
     } else {
-        if (check) k_step2<S, false, true><<<grid, block, kT2Smem, st>>>(a, c);
-        else k_step2<S, false, false><<<grid, block, kT2Smem, st>>>(a, c);
+        if (check) k_step2<S, false, true, false><<<grid, block, kT2Smem, st>>>(a, c);
+        else k_step2<S, false, false, false><<<grid, block, kT2Smem, st>>>(a, c);
     }
     return cudaGetLastError();
 }
