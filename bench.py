@@ -43,12 +43,12 @@ FALLBACK_HBM_GBS = 6800.0
 # (FP32 two-step kernel): bytes per lattice update = this / steps per launch.
 BYTES_PER_LAUNCH_NODE = {"f64": 8 * 8 * 2 + 2 * 8, "f32": 8 * 4 * 2 + 2 * 4, "f16s": (8 * 2 + 2 * 4) * 2 + 2 * 4}
 FORCE_SEED = 0x2208_14870
-# FP64 storage runs its collision on the FP64 pipe: 48 FP64 instructions per
-# lattice update (ncu: 30 DADD, 11 DMUL, 7 DFMA per node), i.e. 55 flops.
+# FP64 storage runs its collision on the FP64 pipe: 42 FP64 instructions per
+# lattice update (ncu: 28 DADD, 5 DMUL, 9 DFMA per node), i.e. 51 flops.
 # Every FP64 instruction takes one slot of the pipe, whose nominal rate on
 # GB300 is 1.25 TFLOP/s counting an FMA as 2 flops, i.e. 625 G instructions/s.
-FP64_INSTR_PER_LUP = 48
-FP64_FLOPS_PER_LUP = 55
+FP64_INSTR_PER_LUP = 42
+FP64_FLOPS_PER_LUP = 51
 FP64_PEAK_GINST = 625.0
 # DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype
 # and steps per launch,
@@ -57,10 +57,10 @@ FP64_PEAK_GINST = 625.0
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32_x2": {"bytes_per_launch": (674.817792e6 + 494.865920e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
-    "f32_x1": {"bytes_per_launch": (671.175936e6 + 486.552320e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
-    "f16s_x1": {"bytes_per_launch": (536.991232e6 + 368.358912e6) * 16, "kernel_hash": "f278ab2b85b36eab"},
-    "f16s_x2": {"bytes_per_launch": (539.921920e6 + 366.681088e6) * 16, "kernel_hash": "fde7484b5d564601"},
+    "f32_x2": {"bytes_per_launch": (674.736640e6 + 492.960768e6) * 16, "kernel_hash": "df0adfad2f8f1b13"},
+    "f32_x1": {"bytes_per_launch": (671.258624e6 + 486.573056e6) * 16, "kernel_hash": "df0adfad2f8f1b13"},
+    "f16s_x1": {"bytes_per_launch": (536.991488e6 + 368.034560e6) * 16, "kernel_hash": "df0adfad2f8f1b13"},
+    "f16s_x2": {"bytes_per_launch": (539.921920e6 + 365.056512e6) * 16, "kernel_hash": "df0adfad2f8f1b13"},
 }
 
 
