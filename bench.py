@@ -416,16 +416,27 @@ def run_e2e(args, gx, gy, torch, P, ws, dist):
     outs = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(5)]
     res = np.zeros(5)
 
+    parts = np.zeros(4)
+
     def step():
+        # every call returns after its work is done (the library synchronises
+        # its stream), so the host clock between calls splits the step
+        t = [time.perf_counter()]
         P.lbm_set_force(lat.ctx, hgx.data_ptr(), hgy.data_ptr())
+        t.append(time.perf_counter())
         P.lbm_reset(lat.ctx)
         P.lbm_iterate_checked(lat.ctx, args.iters, args.check_every, res.ctypes.data)
+        t.append(time.perf_counter())
         P.lbm_get_displacement(lat.ctx, outs[0].data_ptr(), outs[1].data_ptr())
+        t.append(time.perf_counter())
         P.lbm_get_stress(lat.ctx, outs[2].data_ptr(), outs[3].data_ptr(), outs[4].data_ptr())
+        t.append(time.perf_counter())
+        parts[:] += np.diff(t)
 
     for _ in range(args.e2e_warmup):
         step()
     torch.cuda.synchronize()
+    parts[:] = 0.0
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
@@ -442,7 +453,9 @@ def run_e2e(args, gx, gy, torch, P, ws, dist):
             "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 5 * n * n * 8 + 5 * 8,
             "steps": args.e2e_steps, "ms_per_step": dt / args.e2e_steps * 1e3,
             "api": "lbm_set_force(host) + lbm_reset + lbm_iterate_checked + "
-                   "lbm_get_displacement/lbm_get_stress(host)"}
+                   "lbm_get_displacement/lbm_get_stress(host)",
+            "parts_ms": dict(zip(("set_force", "reset_iterate", "get_displacement", "get_stress"),
+                                 (float(v) for v in parts / args.e2e_steps * 1e3)))}
 
 
 # ---------------------------------------------------------------------------

@@ -63,6 +63,7 @@ struct lbm_ctx {
     double* pinned = nullptr;      // kRes + 2 doubles (pinned host)
     double* staging = nullptr;     // FP64 device staging for host transfers
     int64_t staging_len = 0;
+    bool staged_fields = false;    // staging holds the fields of the current state and force
     int cur = 0;
     int64_t step = 0;
     bool snap_valid = false;
@@ -143,6 +144,7 @@ cudaError_t launch_step(lbm_ctx* c, bool check) {
     if (e == cudaSuccess) {
         c->cur ^= 1;
         c->step += 1;
+        c->staged_fields = false;
     }
     return e;
 }
@@ -158,6 +160,7 @@ cudaError_t launch_step2(lbm_ctx* c, bool check) {
     if (e == cudaSuccess) {
         c->cur ^= 1;
         c->step += 2;
+        c->staged_fields = false;
     }
     return e;
 }
@@ -181,6 +184,21 @@ cudaError_t run_window(lbm_ctx* c, int64_t to_check) {
     return e == cudaSuccess ? launch_step(c, true) : e;
 }
 
+cudaError_t launch_fields(lbm_ctx* c, double* out);
+int ensure_staging(lbm_ctx* c, int64_t len);
+
+// The five FP64 field planes of the current state in the staging buffer,
+// computed once per state: lbm_get_displacement and lbm_get_stress of the
+// same state share one field recovery.
+int stage_fields(lbm_ctx* c) {
+    if (c->staged_fields) return LBM_OK;
+    int rc = ensure_staging(c, 5 * c->n);
+    if (rc) return rc;
+    CK(launch_fields(c, c->staging));
+    c->staged_fields = true;
+    return LBM_OK;
+}
+
 cudaError_t launch_fields(lbm_ctx* c, double* out) {
     const StepParams a = params(c, c->cur);
     const Coef<double> cd = coef<double>(c->rates);
@@ -192,6 +210,7 @@ cudaError_t launch_fields(lbm_ctx* c, double* out) {
 }
 
 int ensure_staging(lbm_ctx* c, int64_t len) {
+    c->staged_fields = false;   // every caller overwrites the staging buffer
     if (c->staging_len >= len) return LBM_OK;
     if (c->staging) {
         CK(cudaStreamSynchronize(c->stream));
@@ -235,6 +254,7 @@ int half_exponent(const lbm_ctx* c, double gmax) { return f16s_exponent(gmax, c-
 // Switch the FP16 scale to 2^e, rescaling the stored deviations if asked.
 int set_half_exponent(lbm_ctx* c, int e, bool rescale) {
     if (e == c->hexp) return LBM_OK;
+    c->staged_fields = false;
     if (rescale) {
         const float factor = std::ldexp(1.0f, e - c->hexp);
         k_rescale_half<<<1024, 256, 0, c->stream>>>(static_cast<__half*>(c->pop[c->cur]),
@@ -271,6 +291,7 @@ int update_half_scale(lbm_ctx* c, const double* gx_dev, const double* gy_dev) {
 }
 
 int set_force_dev(lbm_ctx* c, const double* gx, const double* gy) {
+    c->staged_fields = false;
     if (c->dtype == LBM_F64) {
         CK(cudaMemcpyAsync(c->force, gx, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(static_cast<double*>(c->force) + c->plane, gy, c->n * sizeof(double),
@@ -550,6 +571,7 @@ int lbm_reset(lbm_ctx* c) {
     c->step = 0;
     c->snap_valid = false;
     c->state_zero = true;
+    c->staged_fields = false;
     if (c->dtype == LBM_F16S && c->gmax > 0.0) {
         rc = set_half_exponent(c, half_exponent(c, c->gmax), false);
         if (rc) return rc;
@@ -665,9 +687,8 @@ int lbm_get_displacement(lbm_ctx* c, double* ux, double* uy) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!ux || !uy) return fail(LBM_ERR_ARG, "lbm_get_displacement: null pointer");
-    rc = ensure_staging(c, 5 * c->n);
+    rc = stage_fields(c);
     if (rc) return rc;
-    CK(launch_fields(c, c->staging));
     CK(cudaMemcpyAsync(ux, c->staging, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(uy, c->staging + c->n, c->n * sizeof(double), cudaMemcpyDeviceToHost,
                        c->stream));
@@ -679,9 +700,8 @@ int lbm_get_stress(lbm_ctx* c, double* sxx, double* syy, double* sxy) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!sxx || !syy || !sxy) return fail(LBM_ERR_ARG, "lbm_get_stress: null pointer");
-    rc = ensure_staging(c, 5 * c->n);
+    rc = stage_fields(c);
     if (rc) return rc;
-    CK(launch_fields(c, c->staging));
     double* outs[3] = {sxx, syy, sxy};
     for (int k = 0; k < 3; ++k)
         CK(cudaMemcpyAsync(outs[k], c->staging + (2 + k) * c->n, c->n * sizeof(double),

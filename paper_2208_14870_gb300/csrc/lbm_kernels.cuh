@@ -535,8 +535,12 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
     }
 }
 
+#ifndef LBM_MINB_T2_CHECK
+#define LBM_MINB_T2_CHECK 3
+#endif
 template <int S, bool GEN, bool CHECK, bool ANY>
-__global__ void __launch_bounds__(kT2Threads, CHECK ? 2 : (S == S_F16S ? LBM_MINB_T2_F16S : LBM_MINB_T2))
+__global__ void __launch_bounds__(kT2Threads,
+                                  CHECK ? LBM_MINB_T2_CHECK : (S == S_F16S ? LBM_MINB_T2_F16S : LBM_MINB_T2))
 k_step2(const StepParams a, const Coef<float> c) {
     extern __shared__ float t2_smem[];
     const int ntx = (a.nx + kT2OX - 1) / kT2OX;

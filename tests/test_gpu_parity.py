@@ -347,3 +347,39 @@ def test_force_correction_matches_oracle(dtype, tol):
         st, iters, r = lat.solve(1e-14 if dtype == "f64" else 2e-9, 10_000_000, 200)
         assert st == P.LBM_OK
         assert rel(lat.fields()[:2], exact[:2]) < tol
+
+
+def test_host_field_getters_follow_every_state_change():
+    """lbm_get_displacement and lbm_get_stress share one field recovery per
+    state; after a step, a new force, a reset, a population read-back or a
+    population load they must show the new state (each checked against the
+    device-side recovery, which never uses the shared one)."""
+    lam, mu = W.lame_2d(1.0, 0.3)
+    nx, ny = 96, 40
+    pw = W.random_force(nx, ny, 6, 4, seed=21)
+    gx, gy = W.random_force_grid(pw)
+    with Lattice(nx, ny, lam, mu, "f32") as lat:
+        dev = torch.empty(5 * nx * ny, dtype=torch.float64, device="cuda")
+
+        def check():
+            host = np.concatenate([lat.displacement(), lat.stress()])
+            want = lat.fields_device(dev).view(5, ny, nx).cpu().numpy()
+            assert np.array_equal(host, want)
+            return host
+
+        lat.set_force(gx, gy)
+        lat.iterate(7)
+        a = check()
+        lat.iterate(3)
+        b = check()
+        assert not np.array_equal(a, b)
+        lat.set_force(0.5 * gx, 0.5 * gy)          # u = m10 + g/2 changes with g
+        c = check()
+        assert not np.array_equal(b, c)
+        f = lat.populations()
+        check()
+        lat.reset()
+        z = check()                               # zero state: u = g/2, sigma = 0
+        assert np.allclose(z[0], 0.25 * gx) and np.max(np.abs(z[2:])) == 0.0
+        lat.set_populations(f)
+        assert np.array_equal(check(), c)
