@@ -201,7 +201,7 @@ def run_reference(args, ws, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(args),
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_description()},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -231,7 +231,30 @@ def cpu_baseline(args):
     dt = time.perf_counter() - t0
     return {"value": m * m * it / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": "%dx%d lattice, same force recipe, %d steps, single-threaded FP64 C oracle "
-                      "(%.1f s)" % (m, m, it, dt)}
+                      "(%.1f s)" % (m, m, it, dt),
+            "host": host_description()}
+
+
+def host_description():
+    """The host the CPU baseline ran on: logical cores and CPU model."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "cpu implementer") and not model:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"logical_cores": os.cpu_count(), "machine": platform.machine(), "cpu": model}
 
 
 # ---------------------------------------------------------------------------
