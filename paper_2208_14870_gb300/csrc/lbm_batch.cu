@@ -118,14 +118,23 @@ extern "C" int lbm_batch_solve(int count, const lbm_problem* probs, int dtype, d
         }
         chosen_V = V;
         grid = V ? eng.grid_blocks(V) : 0;
-        for (int i = 0; i < count && rc == LBM_OK; ++i) {
-            const HostProb& hp = eng.prob(slot[i]);
-            lbm_result& r = results[i];
-            r.status = hp.status;
-            r.iters = hp.steps;
-            r.residual = hp.residual;
-            lups += hp.lups;
-            rc = eng.recover(slot[i], r.ux, r.uy, r.sxx, r.syy, r.sxy, &err);
+        if (rc == LBM_OK) {
+            // problems whose caller wants fields, recovered together
+            std::vector<int> want;
+            std::vector<double*> outs;
+            for (int i = 0; i < count; ++i) {
+                const HostProb& hp = eng.prob(slot[i]);
+                lbm_result& r = results[i];
+                r.status = hp.status;
+                r.iters = hp.steps;
+                r.residual = hp.residual;
+                lups += hp.lups;
+                double* o[5] = {r.ux, r.uy, r.sxx, r.syy, r.sxy};
+                if (!(o[0] || o[1] || o[2] || o[3] || o[4])) continue;
+                want.push_back(slot[i]);
+                outs.insert(outs.end(), o, o + 5);
+            }
+            rc = eng.recover_many((int)want.size(), want.data(), outs.data(), &err);
         }
     }
     cudaStreamDestroy(st);

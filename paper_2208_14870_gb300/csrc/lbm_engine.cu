@@ -51,6 +51,7 @@ ArenaEngine::~ArenaEngine() {
     if (h_acc_) cudaFreeHost(h_acc_);
     if (h_tiles_) cudaFreeHost(h_tiles_);
     if (h_force_) cudaFreeHost(h_force_);
+    if (h_fields_) cudaFreeHost(h_fields_);
     if (ev0_) cudaEventDestroy(ev0_);
     if (ev1_) cudaEventDestroy(ev1_);
 }
@@ -403,21 +404,9 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
     return LBM_OK;
 }
 
-int ArenaEngine::recover(int slot, double* ux, double* uy, double* sxx, double* syy, double* sxy,
-                         std::string* err) {
+// FP64 fields of problem `slot` into device memory dst (5 planes of n).
+cudaError_t ArenaEngine::launch_fields(int slot, double* dst) {
     const HostProb& p = probs_[slot];
-    if (p.state == P_FREE) {
-        if (err) *err = "recover: empty slot";
-        return LBM_ERR_STATE;
-    }
-    if (d_fields_cap_ < 5 * p.n) {
-        if (d_fields_) {
-            ECK(cudaStreamSynchronize(st_));
-            cudaFree(d_fields_);
-        }
-        ECK(cudaMalloc(&d_fields_, sizeof(double) * 5 * p.n));
-        d_fields_cap_ = 5 * p.n;
-    }
     StepParams a{};
     a.nx = p.nx;
     a.ny = p.ny;
@@ -442,15 +431,85 @@ int ArenaEngine::recover(int slot, double* ux, double* uy, double* sxx, double* 
     c.bs = 1.0 - 0.5 * ws;
     c.bd = 1.0 - 0.5 * wd;
     c.theta = theta;
-    cudaError_t e = dtype_ == S_F16S ? Ops<S_F16S>::fields(a, c, (float)theta, d_fields_, st_)
-                                     : Ops<S_F32>::fields(a, c, (float)theta, d_fields_, st_);
-    ECK(e);
+    return dtype_ == S_F16S ? Ops<S_F16S>::fields(a, c, (float)theta, dst, st_)
+                            : Ops<S_F32>::fields(a, c, (float)theta, dst, st_);
+}
+
+int ArenaEngine::ensure_fields_buffer(int64_t len, std::string* err) {
+    if (d_fields_cap_ >= len) return LBM_OK;
+    if (d_fields_) {
+        ECK(cudaStreamSynchronize(st_));
+        cudaFree(d_fields_);
+        d_fields_ = nullptr;
+        d_fields_cap_ = 0;
+    }
+    ECK(cudaMalloc(&d_fields_, sizeof(double) * len));
+    d_fields_cap_ = len;
+    return LBM_OK;
+}
+
+int ArenaEngine::recover(int slot, double* ux, double* uy, double* sxx, double* syy, double* sxy,
+                         std::string* err) {
+    const HostProb& p = probs_[slot];
+    if (p.state == P_FREE) {
+        if (err) *err = "recover: empty slot";
+        return LBM_ERR_STATE;
+    }
+    int rc = ensure_fields_buffer(5 * p.n, err);
+    if (rc) return rc;
+    ECK(launch_fields(slot, d_fields_));
     double* outs[5] = {ux, uy, sxx, syy, sxy};
     for (int i = 0; i < 5; ++i)
         if (outs[i])
             ECK(cudaMemcpyAsync(outs[i], d_fields_ + i * p.n, sizeof(double) * p.n,
                                 cudaMemcpyDeviceToHost, st_));
     ECK(cudaStreamSynchronize(st_));
+    return LBM_OK;
+}
+
+int ArenaEngine::recover_many(int count, const int* slots, double* const* outs, std::string* err) {
+    // Problems are packed into blocks of kRecoverBlock doubles: one field
+    // launch per problem into a device block, one copy of the block into a
+    // pinned host block, one synchronisation, then host copies into the
+    // callers' arrays.  A problem larger than a block goes alone.
+    constexpr int64_t kRecoverBlock = int64_t(4) << 20;   // 32 MB of FP64
+    for (int i = 0; i < count; ++i)
+        if (probs_[slots[i]].state == P_FREE) {
+            if (err) *err = "recover: empty slot";
+            return LBM_ERR_STATE;
+        }
+    int rc = ensure_fields_buffer(kRecoverBlock, err);
+    if (rc) return rc;
+    if (!h_fields_) {
+        ECK(cudaMallocHost(&h_fields_, sizeof(double) * kRecoverBlock));
+    }
+    for (int i = 0; i < count;) {
+        if (5 * probs_[slots[i]].n > kRecoverBlock) {
+            double* const* o = outs + 5 * (int64_t)i;
+            rc = recover(slots[i], o[0], o[1], o[2], o[3], o[4], err);
+            if (rc) return rc;
+            ++i;
+            continue;
+        }
+        int j = i;
+        int64_t used = 0;
+        for (; j < count && 5 * probs_[slots[j]].n <= kRecoverBlock - used; ++j) {
+            ECK(launch_fields(slots[j], d_fields_ + used));
+            used += 5 * probs_[slots[j]].n;
+        }
+        ECK(cudaMemcpyAsync(h_fields_, d_fields_, sizeof(double) * used, cudaMemcpyDeviceToHost, st_));
+        ECK(cudaStreamSynchronize(st_));
+        int64_t off = 0;
+        for (int q = i; q < j; ++q) {
+            const int64_t n = probs_[slots[q]].n;
+            for (int f = 0; f < 5; ++f) {
+                double* dst = outs[5 * (int64_t)q + f];
+                if (dst) std::memcpy(dst, h_fields_ + off + f * n, sizeof(double) * n);
+            }
+            off += 5 * n;
+        }
+        i = j;
+    }
     return LBM_OK;
 }
 

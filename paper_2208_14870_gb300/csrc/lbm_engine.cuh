@@ -58,6 +58,9 @@ public:
     // (nullable), FP64, lattice units.
     int recover(int slot, double* ux, double* uy, double* sxx, double* syy, double* sxy,
                 std::string* err);
+    // The same for count problems at once; outs holds 5 nullable host arrays
+    // (ux, uy, sxx, syy, sxy) per problem.  Few copies and synchronisations.
+    int recover_many(int count, const int* slots, double* const* outs, std::string* err);
     void release(int slot);
     const HostProb& prob(int slot) const { return probs_[slot]; }
     int running() const { return nrunning_; }
@@ -71,6 +74,8 @@ public:
 
 private:
     int upload_tiles(int V, std::string* err);
+    cudaError_t launch_fields(int slot, double* dst);
+    int ensure_fields_buffer(int64_t len, std::string* err);
     int ensure_graph(int V, std::string* err);
 
     int dtype_ = S_F32;
@@ -97,6 +102,7 @@ private:
     int64_t h_force_cap_ = 0;
     double* d_fields_ = nullptr;      // FP64 staging for recovery
     int64_t d_fields_cap_ = 0;
+    double* h_fields_ = nullptr;      // pinned block for recover_many
     cudaGraphExec_t graph_[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool graph_failed_[5] = {false, false, false, false, false};
     cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;

@@ -134,3 +134,23 @@ def test_batch_two_step_tiles_match_one_step_tiles(dtype, monkeypatch):
             assert np.array_equal(a["fields"], b["fields"])
         else:
             assert rel_per_field(b["fields"], a["fields"]) < 2e-3
+
+
+def test_batch_recovery_packs_small_and_large_problems():
+    """Fields come back through packed copies (several problems per pinned
+    block) and, for a problem larger than a block, on their own; both must
+    equal a single lattice after the same steps (FP32: same bits), and a
+    problem without output arrays is skipped without disturbing the rest."""
+    sizes = [(1024, 1024), (40, 30), (300, 200), (33, 17)]
+    probs = make_problems(sizes, seed=17)
+    results, _ = P.batch_solve([p[:6] for p in probs], dtype="f32", tol=0.0, check_every=100,
+                               max_iters=200)
+    for (nx, ny, lam, mu, gx, gy, pw), r in zip(probs, results):
+        assert r["status"] == P.LBM_ERR_NOT_CONVERGED and r["iters"] == 200
+        with P.Lattice(nx, ny, lam, mu, "f32") as lat:
+            lat.set_force(gx, gy)
+            lat.iterate(200)
+            assert np.array_equal(r["fields"], lat.fields()), (nx, ny)
+    res_nf, _ = P.batch_solve([p[:6] for p in probs], dtype="f32", tol=0.0, check_every=100,
+                              max_iters=200, fields=False)
+    assert all("fields" not in r and r["iters"] == 200 for r in res_nf)
