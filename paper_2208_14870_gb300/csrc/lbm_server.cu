@@ -94,7 +94,7 @@ struct lbm_server {
 
     void run();
     int admit_locked();
-    void retire(int a, int slot, std::unique_lock<std::mutex>& lk);
+    void retire(int a, const std::vector<int>& slots, std::unique_lock<std::mutex>& lk);
 };
 
 void lbm_server::run() {
@@ -140,7 +140,7 @@ void lbm_server::run() {
                 reqs.erase(slot_owner[a][s]);
                 slot_owner[a].erase(s);
             }
-            for (int s : done) retire(a, s, lk);
+            if (!done.empty()) retire(a, done, lk);
         }
     }
     if (failed != LBM_OK) {
@@ -187,37 +187,46 @@ int lbm_server::admit_locked() {
     return LBM_OK;
 }
 
-void lbm_server::retire(int a, int slot, std::unique_lock<std::mutex>& lk) {
-    const uint64_t t = slot_owner[a][slot];
-    Request& r = *reqs[t];
-    const HostProb& p = arena[a]->prob(slot);
-    r.status = p.status;
-    r.iters = p.steps;
-    r.residual = p.residual;
-    lups += p.lups;
-    r.fields.assign((size_t)5 * r.nx * r.ny, 0.0);
-    const int64_t n = (int64_t)r.nx * r.ny;
+// Finished problems of one arena: their fields are recovered together (one
+// packed copy per block of problems), then each request is completed.
+void lbm_server::retire(int a, const std::vector<int>& slots, std::unique_lock<std::mutex>& lk) {
+    std::vector<double*> outs;
+    outs.reserve(5 * slots.size());
+    for (int slot : slots) {
+        Request& r = *reqs[slot_owner[a][slot]];
+        const int64_t n = (int64_t)r.nx * r.ny;
+        r.fields.assign((size_t)5 * n, 0.0);
+        double* f = r.fields.data();
+        for (int k = 0; k < 5; ++k) outs.push_back(f + k * n);
+    }
     std::string err;
-    double* f = r.fields.data();
     lk.unlock();
-    int rc = arena[a]->recover(slot, f, f + n, f + 2 * n, f + 3 * n, f + 4 * n, &err);
+    const int rc = arena[a]->recover_many((int)slots.size(), slots.data(), outs.data(), &err);
     lk.lock();
     if (rc != LBM_OK) {
-        r.status = rc;
         failed = rc;
         fail_msg = err;
     }
-    arena[a]->release(slot);
-    slot_owner[a].erase(slot);
-    if (r.cancelled) {
-        reqs.erase(t);
-        return;
+    for (int slot : slots) {
+        const uint64_t t = slot_owner[a][slot];
+        Request& r = *reqs[t];
+        const HostProb& p = arena[a]->prob(slot);
+        r.status = rc != LBM_OK ? rc : p.status;
+        r.iters = p.steps;
+        r.residual = p.residual;
+        lups += p.lups;
+        arena[a]->release(slot);
+        slot_owner[a].erase(slot);
+        if (r.cancelled) {
+            reqs.erase(t);
+            continue;
+        }
+        r.state = R_DONE;
+        r.t_done = clk::now();
+        t_last_done = r.t_done;
+        latencies_ms.push_back(ms_between(r.t_submit, r.t_done));
+        ++completed;
     }
-    r.state = R_DONE;
-    r.t_done = clk::now();
-    t_last_done = r.t_done;
-    latencies_ms.push_back(ms_between(r.t_submit, r.t_done));
-    ++completed;
     cv_done.notify_all();
 }
 
