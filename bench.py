@@ -57,10 +57,10 @@ FP64_PEAK_GINST = 625.0
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32_x2": {"bytes_per_launch": (674.736640e6 + 492.960768e6) * 16, "kernel_hash": "df0adfad2f8f1b13"},
-    "f32_x1": {"bytes_per_launch": (671.258624e6 + 486.573056e6) * 16, "kernel_hash": "df0adfad2f8f1b13"},
-    "f16s_x1": {"bytes_per_launch": (536.991488e6 + 368.034560e6) * 16, "kernel_hash": "df0adfad2f8f1b13"},
-    "f16s_x2": {"bytes_per_launch": (539.921920e6 + 365.056512e6) * 16, "kernel_hash": "df0adfad2f8f1b13"},
+    "f32_x2": {"bytes_per_launch": (674.853888e6 + 493.407488e6) * 16, "kernel_hash": "ca17dcca98b62a75"},
+    "f32_x1": {"bytes_per_launch": (671.173632e6 + 485.997824e6) * 16, "kernel_hash": "ca17dcca98b62a75"},
+    "f16s_x1": {"bytes_per_launch": (536.988928e6 + 367.846144e6) * 16, "kernel_hash": "ca17dcca98b62a75"},
+    "f16s_x2": {"bytes_per_launch": (539.984384e6 + 364.976384e6) * 16, "kernel_hash": "ca17dcca98b62a75"},
 }
 
 
@@ -664,8 +664,8 @@ def main():
                     help="extra storage variants; a suffix xK fixes K steps per launch")
     ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--e2e-warmup", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-warmup", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--ref-iters", type=int, default=40)
