@@ -23,6 +23,7 @@ import hashlib
 import io
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -52,15 +53,16 @@ FP64_FLOPS_PER_LUP = 51
 FP64_PEAK_GINST = 625.0
 # DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype
 # and steps per launch,
-# with the hash of the kernel sources it was taken on (null once they change).
+# with the hash of the kernel code it was taken on (null once the code changes;
+# comments do not count).
 # Captured on 4096^2 (profiles/k_step*_4096_full.md) and scaled by the node
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32_x2": {"bytes_per_launch": (674.853888e6 + 493.407488e6) * 16, "kernel_hash": "ca17dcca98b62a75"},
-    "f32_x1": {"bytes_per_launch": (671.173632e6 + 485.997824e6) * 16, "kernel_hash": "ca17dcca98b62a75"},
-    "f16s_x1": {"bytes_per_launch": (536.988928e6 + 367.846144e6) * 16, "kernel_hash": "ca17dcca98b62a75"},
-    "f16s_x2": {"bytes_per_launch": (539.984384e6 + 364.976384e6) * 16, "kernel_hash": "ca17dcca98b62a75"},
+    "f32_x2": {"bytes_per_launch": (674.853888e6 + 493.407488e6) * 16, "kernel_hash": "357960238ea21163"},
+    "f32_x1": {"bytes_per_launch": (671.173632e6 + 485.997824e6) * 16, "kernel_hash": "357960238ea21163"},
+    "f16s_x1": {"bytes_per_launch": (536.988928e6 + 367.846144e6) * 16, "kernel_hash": "357960238ea21163"},
+    "f16s_x2": {"bytes_per_launch": (539.984384e6 + 364.976384e6) * 16, "kernel_hash": "357960238ea21163"},
 }
 
 
@@ -72,15 +74,25 @@ def kernel_source(text: str) -> str:
     return text[a:b]
 
 
-def kernel_hash() -> str:
-    """Hash of the stream-collide kernel's source: per-node arithmetic
-    (lbm_core.cuh), the kernel section of lbm_kernels.cuh and its launcher."""
+def code_only(text: str) -> str:
+    """C/CUDA source without comments and with whitespace collapsed."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_hash(read=None) -> str:
+    """Hash of the code (comments and layout ignored) of the stream-collide
+    kernels: per-node arithmetic (lbm_core.cuh), lbm_kernels.cuh and the
+    launchers.  `read(name)` returns a file's text (default: this tree)."""
     d = os.path.join(ROOT, "paper_2208_14870_gb300", "csrc")
+    if read is None:
+        def read(name):
+            with open(os.path.join(d, name)) as fh:
+                return fh.read()
     h = hashlib.sha256()
-    h.update(open(os.path.join(d, "lbm_core.cuh"), "rb").read())
-    h.update(kernel_source(open(os.path.join(d, "lbm_kernels.cuh")).read()).encode())
-    h.update(open(os.path.join(d, "lbm_ops.cuh"), "rb").read())
-    h.update(open(os.path.join(d, "lbm_step_f32.cu"), "rb").read())
+    for name in ("lbm_core.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_step_f32.cu", "lbm_step_f16s.cu"):
+        h.update(code_only(read(name)).encode())
     return h.hexdigest()[:16]
 
 

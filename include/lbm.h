@@ -278,7 +278,7 @@ typedef struct lbm_result {
 
 typedef struct lbm_batch_report {
     int tile_v;                 /* tile code used: 1, 2, 4 (warps of 32 columns) or LBM_TILE_TWO_STEP */
-    int blocks;                 /* persistent grid size */
+    int blocks;                 /* grid of the persistent chunk kernel */
     int64_t chunks;             /* chunk launches */
     int64_t lattice_updates;    /* sum over problems of nodes x steps */
     double device_ms;           /* device time of the chunks (CUDA events) */

@@ -74,7 +74,8 @@ struct StepParams {
     float hinv;             // 1 / hscale
     void* snap;             // residual: u_x, u_y snapshot, 2 planes of nx*ny (type U)
     double* partials;       // residual: kRes doubles per block
-    unsigned int* counter;  // residual: blocks finished (reset by the last block)
+    unsigned int* counter;  // residual: blocks finished, reset by the last block; null:
+                            // blocks only write partials (k_residual_finish combines them)
     double* result;         // residual: kRes doubles
 };
 
@@ -172,9 +173,11 @@ __device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
 // snapshot type U (max|du|, max|u|, sum du^2, sum u^2, non-finite flag); a
 // warp combines them in U (maxima are exact; FP32 sums of at most 32*V terms
 // carry a relative error below 1e-6), then the block and the grid combine
-// the warp results in FP64.  The grid-level pass is done by the last block to
-// finish (counted with an atomic), which also resets the counter for the next
-// check.
+// the warp results in FP64.  With a counter, the grid-level pass is done by
+// the last block to finish (counted with an atomic), which also resets the
+// counter for the next check; without one (the library's own check launches)
+// the blocks stop after writing their partials and k_residual_finish combines
+// them in a separate launch.
 template <typename U>
 __device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) {
     __shared__ double sh[kRes][kThreads / 32];
@@ -674,7 +677,8 @@ __global__ void k_force_correct(const double* gx, const double* gy, double* ox, 
 template <int S>
 struct Ops {
     using T = typename StoreT<S>::T;
-    // check_blocks: grid of the persistent CHECK launch (<= partials slots)
+    // check_blocks: grid cap of the CHECK launch (<= partials slots); one
+    // block per tile below it
     static cudaError_t step(const StepParams& a, const Coef<T>& c, int V, bool gen, bool check,
                             int check_blocks, cudaStream_t st);
     static cudaError_t fields(const StepParams& a, const Coef<double>& c, T theta, double* out,
