@@ -651,6 +651,9 @@ def run_served(args, P):
             "requests": len(reqs), "converged": statuses.count(0),
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"],
             "p99_ms": st["p99_ms"], "peak_running": st["peak_running"],
+            "device_s": st["device_ms"] / 1e3, "chunks": st["chunks"], "tile_v": st["tile_v"],
+            "lattice_updates": st["lattice_updates"],
+            "glups_device": st["lattice_updates"] / max(st["device_ms"], 1e-9) / 1e6,
             "plain_solves_per_s": len(reqs) / (done - 0.0) if done > 0 else None,
             "plain_p50_ms": float(np.percentile(lat, 50)), "plain_p95_ms": float(np.percentile(lat, 95)),
             "plain_p99_ms": float(np.percentile(lat, 99)),
