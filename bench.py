@@ -275,13 +275,24 @@ def host_description():
 
 def launches_per_iterate(iters, check_every, spl):
     """Stream-collide launches of lbm_iterate_checked(iters, check_every) from
-    step 0: each window is check_every - 1 plain steps (paired when two steps
-    run per launch) and the check step (the second of a pair)."""
+    step 0: each window is check_every - 1 plain steps grouped into launches of
+    spl steps (the remainder in shorter ones) and ends with the check step,
+    the last step of a launch of min(spl, check_every) steps."""
     def plain(m):
-        return m // 2 + m % 2 if spl == 2 else m
+        if spl == 3:
+            if m % 3 == 1 and m >= 4:
+                return (m - 4) // 3 + 2
+            return m // 3 + (1 if m % 3 else 0)
+        if spl == 2:
+            return m // 2 + m % 2
+        return m
+
+    def window(w):
+        last = min(spl, w)
+        return plain(w - last) + 1
     total, left = 0, iters
     while left >= check_every:
-        total += plain(check_every - 2) + 1 if (spl == 2 and check_every >= 2) else plain(check_every - 1) + 1
+        total += window(check_every)
         left -= check_every
     return total + plain(left)
 
@@ -675,7 +686,7 @@ def main():
                     help="steps per stream-collide launch of the main line (default: the library's choice)")
     ap.add_argument("--f64-iters", type=int, default=100,
                     help="pseudo-time steps per benchmark step of the FP64 variant")
-    ap.add_argument("--variants", nargs="*", default=["f16s", "f32x1", "f16sx1", "f64"],
+    ap.add_argument("--variants", nargs="*", default=["f16s", "f32x2", "f32x1", "f16sx2", "f16sx1", "f64"],
                     help="extra storage variants; a suffix xK fixes K steps per launch")
     ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")
     ap.add_argument("--no-e2e", action="store_true")

@@ -116,23 +116,24 @@ void lbm_destroy(lbm_ctx *ctx);
  * all later work of this context.  The caller keeps ownership of the stream. */
 int lbm_set_stream(lbm_ctx *ctx, void *stream);
 
-/* Pseudo-time steps per stream-collide launch: 1 or 2.  With 2, one launch
- * runs two consecutive steps of Algorithm 1 (Sec. 3.3, Eqs. collision and
- * streaming): the first step's post-collision state of a tile and its one-node
- * halo stays on chip in FP32, so the populations cross device memory once per
- * two steps.  A residual check (lbm_iterate_checked, lbm_solve) falls on the
- * second step of a pair.  With LBM_F32 storage the arithmetic per node is
- * unchanged and the state after every launch equals that of the same steps
- * taken one per launch, bit for bit.  With LBM_F16S storage the intermediate
- * state is not rounded to the FP16 storage format, so results differ from one
- * step per launch by less than that format's rounding (and lie closer to the
- * FP64 result).  Available for LBM_F32 and LBM_F16S storage on any lattice;
- * the default from nx >= 64 and ny >= 24 on (a smaller lattice fills the
- * 64 x 24 on-chip tile more than once and is faster one step per launch).
- * LBM_F64 storage always runs one step per launch.  Paper: the scheme advances
- * one step at a time; the pairing is a schedule of the same steps, not part
- * of the method.
- * Errors: LBM_ERR_ARG (k not 1 or 2, or k = 2 with LBM_F64 storage). */
+/* Pseudo-time steps per stream-collide launch: 1, 2 or 3.  With k > 1, one
+ * launch runs k consecutive steps of Algorithm 1 (Sec. 3.3, Eqs. collision and
+ * streaming): the intermediate post-collision states of a tile and its halo
+ * (one node per extra step) stay on chip in FP32, so the populations cross
+ * device memory once per k steps.  A residual check (lbm_iterate_checked,
+ * lbm_solve) falls on the last step of a launch; steps left over when n is not
+ * a multiple of k run in shorter launches.  With LBM_F32 storage the
+ * arithmetic per node is unchanged and the state after every launch equals
+ * that of the same steps taken one per launch, bit for bit.  With LBM_F16S
+ * storage the intermediate states are not rounded to the FP16 storage format,
+ * so results differ from one step per launch by less than that format's
+ * rounding (and lie closer to the FP64 result).  Available for LBM_F32 and
+ * LBM_F16S storage on any lattice; the default is 3 from nx >= 64 and
+ * ny >= 16 on (a smaller lattice fills the on-chip tile more than once and is
+ * faster one step per launch).  LBM_F64 storage always runs one step per
+ * launch.  Paper: the scheme advances one step at a time; grouping steps into
+ * launches is a schedule of the same steps, not part of the method.
+ * Errors: LBM_ERR_ARG (k outside 1..3, or k > 1 with LBM_F64 storage). */
 int lbm_set_steps_per_launch(lbm_ctx *ctx, int k);
 int lbm_get_steps_per_launch(lbm_ctx *ctx, int *k);
 

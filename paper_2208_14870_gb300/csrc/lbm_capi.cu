@@ -75,8 +75,9 @@ struct lbm_ctx {
     int V = 1;
     size_t bytes = 0;
     int64_t nblocks = 0;           // grid of the residual-check launch
-    int spl = 1;                   // pseudo-time steps per stream-collide launch (1 or 2)
+    int spl = 1;                   // pseudo-time steps per stream-collide launch (1, 2 or 3)
     int64_t nblocks2 = 0;          // grid of the two-step check launch
+    int64_t nblocks3 = 0;          // grid of the three-step check launch
 };
 
 namespace {
@@ -165,22 +166,51 @@ cudaError_t launch_step2(lbm_ctx* c, bool check) {
     return e;
 }
 
-// n plain steps, paired into two-step launches where the context uses them.
+// Three steps in one launch (FP32 or FP16-shifted storage); with check the
+// third step is the residual-check step.
+cudaError_t launch_step3(lbm_ctx* c, bool check) {
+    const StepParams a = params(c, c->cur);
+    cudaError_t e = c->dtype == LBM_F32
+                        ? step3_f32(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks3, c->stream)
+                        : step3_f16s(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks3, c->stream);
+    if (e == cudaSuccess && check) e = finish_residual_launch(c, c->nblocks3);
+    if (e == cudaSuccess) {
+        c->cur ^= 1;
+        c->step += 3;
+        c->staged_fields = false;
+    }
+    return e;
+}
+
+// n plain steps, grouped into launches of c->spl steps; with three steps per
+// launch a remainder of one step is avoided where possible (4 = 2 + 2), since
+// a pair of steps costs about as much as one step alone.
 cudaError_t run_plain(lbm_ctx* c, int64_t n) {
     cudaError_t e = cudaSuccess;
-    if (c->spl == 2)
+    if (c->spl == 3) {
+        const int64_t triples = n % 3 == 1 && n >= 4 ? (n - 4) / 3 : n / 3;
+        for (int64_t i = 0; i < triples && e == cudaSuccess; ++i) e = launch_step3(c, false);
+        n -= 3 * triples;
+    }
+    if (c->spl >= 2)
         for (; n >= 2 && e == cudaSuccess; n -= 2) e = launch_step2(c, false);
     for (; n > 0 && e == cudaSuccess; --n) e = launch_step(c, false);
     return e;
 }
 
-// to_check - 1 plain steps followed by the residual-check step.
+// to_check - 1 plain steps followed by the residual-check step (the last
+// step of the last launch).
 cudaError_t run_window(lbm_ctx* c, int64_t to_check) {
-    if (c->spl == 2 && to_check >= 2) {
-        cudaError_t e = run_plain(c, to_check - 2);
+    cudaError_t e;
+    if (c->spl == 3 && to_check >= 3) {
+        e = run_plain(c, to_check - 3);
+        return e == cudaSuccess ? launch_step3(c, true) : e;
+    }
+    if (c->spl >= 2 && to_check >= 2) {
+        e = run_plain(c, to_check - 2);
         return e == cudaSuccess ? launch_step2(c, true) : e;
     }
-    cudaError_t e = run_plain(c, to_check - 1);
+    e = run_plain(c, to_check - 1);
     return e == cudaSuccess ? launch_step(c, true) : e;
 }
 
@@ -393,7 +423,9 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     c->nblocks = std::min(step_tiles(nx, ny, c->V), kMaxCheckBlocks);
     if (dtype != LBM_F64) {
         c->nblocks2 = std::min(step2_tiles(nx, ny), kMaxCheckBlocks);
-        if (step2_fits(nx, ny)) c->spl = 2;
+        c->nblocks3 = std::min(step3_tiles(nx, ny), kMaxCheckBlocks);
+        if (step3_fits(nx, ny)) c->spl = 3;
+        else if (step2_fits(nx, ny)) c->spl = 2;
     }
 
     const size_t pb = pop_elem_bytes(dtype) * 8 * c->plane;
@@ -413,7 +445,7 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     const size_t snap_bytes = (dtype == LBM_F64 ? sizeof(double) : sizeof(float)) * 2 * c->n;
     if (e == cudaSuccess) e = alloc(&c->snap, snap_bytes);
     if (e == cudaSuccess) e = alloc((void**)&c->partials,
-                                       sizeof(double) * kRes * std::max(c->nblocks, c->nblocks2));
+                                       sizeof(double) * kRes * std::max(c->nblocks, std::max(c->nblocks2, c->nblocks3)));
     if (e == cudaSuccess) e = alloc((void**)&c->result, sizeof(double) * kRes);
     if (e == cudaSuccess) e = alloc((void**)&c->absmax, sizeof(unsigned long long));
     if (e == cudaSuccess) e = alloc((void**)&c->bad, sizeof(unsigned int));
@@ -452,9 +484,10 @@ void lbm_destroy(lbm_ctx* c) {
 int lbm_set_steps_per_launch(lbm_ctx* c, int k) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if (k != 1 && k != 2) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: k must be 1 or 2");
-    if (k == 2 && c->dtype == LBM_F64)
-        return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: two steps per launch need FP32 or FP16-shifted storage");
+    if (k < 1 || k > 3) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: k must be 1, 2 or 3");
+    if (k > 1 && c->dtype == LBM_F64)
+        return fail(LBM_ERR_ARG,
+                    "lbm_set_steps_per_launch: several steps per launch need FP32 or FP16-shifted storage");
     c->spl = k;
     return LBM_OK;
 }

@@ -429,6 +429,7 @@ static_assert(kT2Threads == kThreads, "residual_reduce sizes its scratch by kThr
 template <bool ANY>
 __device__ __forceinline__ int wrap_slot(int v, int n) {
     if (v < 0) v += n;
+    if (ANY && v < 0) v = v % n + n;   // v >= -2 on a lattice of one node
     if (v >= n) v = (!ANY || v < 2 * n) ? v - n : v % n;
     return v;
 }
@@ -552,6 +553,175 @@ k_step2(const StepParams a, const Coef<float> c) {
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
         step2_tile<S, GEN, CHECK, ANY>(a, c, t2_smem, tx, ty, acc);
+        if (t + gridDim.x < ntiles) __syncthreads();   // slots are reused by the next tile
+    }
+    if (CHECK) residual_reduce<float>(a, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Three pseudo-time steps per launch (FP32 or FP16-shifted storage).
+//
+// The two-step scheme carried one step further: a block of 256 threads owns an
+// output tile of kT3OX x kT3OY nodes (60 x 12) and two shared-memory slot
+// arrays A and B of kT3W x kT3H slots (64 x 16, 32 KB each): the tile grown
+// by two nodes on every side.  Step 1 pulls f*(t) from global memory and
+// writes f*(t+1) of every slot to A; step 2 pulls from A and writes f*(t+2)
+// of the slots one node inside the edge to B; step 3 pulls from B and stores
+// f*(t+3) of the tile.  Per node and launch the state crosses HBM once: 72 B
+// (FP32) or 56 B (FP16S) for three lattice updates.  Thread (lane, warp) owns
+// slot columns lane and lane + 32 and rows warp + 8k in all three steps; the
+// per-node arithmetic is the single step's, so FP32 results equal three
+// single-step launches bit for bit (FP16S keeps the two intermediate states
+// in FP32).  CHECK makes the third step the residual-check step.  ANY as for
+// k_step2; the library uses the ANY = false kernel from kT3W x kT3H nodes up.
+#ifndef LBM_T3_RPW
+#define LBM_T3_RPW 2
+#endif
+#ifndef LBM_MINB_T3
+#define LBM_MINB_T3 3
+#endif
+constexpr int kT3Rows = LBM_T3_RPW;             // slot rows per warp
+constexpr int kT3W = 64;                        // slot columns (two per lane)
+constexpr int kT3H = 8 * kT3Rows;               // slot rows
+constexpr int kT3OX = kT3W - 4, kT3OY = kT3H - 4;
+constexpr int kT3Smem = 2 * 8 * kT3H * kT3W * (int)sizeof(float);
+
+template <int S, bool GEN, bool CHECK, bool ANY>
+__device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float>& c, float* smA,
+                                           int tx, int ty, float acc[kRes]) {
+    constexpr int PL = kT3H * kT3W;             // shared-memory plane
+    float* smB = smA + 8 * PL;
+    const int nx = a.nx, ny = a.ny;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = tx * kT3OX - 2, y0 = ty * kT3OY - 2;   // node of slot (0, 0)
+    const float* __restrict__ gxp = static_cast<const float*>(a.gx);
+    const float* __restrict__ gyp = static_cast<const float*>(a.gy);
+    int X[2], XM[2], XP[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int x = wrap_slot<ANY>(x0 + lane + 32 * j, nx);
+        X[j] = x;
+        XM[j] = wrap_dec(x, nx);
+        XP[j] = wrap_inc(x, nx);
+    }
+    float gx[kT3Rows][2], gy[kT3Rows][2];
+    // Step 1: f*(t+1) of every slot into A.
+#pragma unroll
+    for (int k = 0; k < kT3Rows; ++k) {
+        const int r = warp + 8 * k;
+        const int y = wrap_slot<ANY>(y0 + r, ny);
+        const int64_t r0 = (int64_t)y * nx;
+        const int64_t rm = (int64_t)wrap_dec(y, ny) * nx, rp = (int64_t)wrap_inc(y, ny) * nx;
+        float f[2][8];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            gather<S>(a, r0, rm, rp, X[j], XM[j], XP[j], f[j], c.theta);
+            gx[k][j] = ldg(gxp + r0 + X[j]);
+            gy[k][j] = ldg(gyp + r0 + X[j]);
+        }
+        float* s = smA + r * kT3W + lane;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float u, v, fs[8];
+            populations(collide<float, GEN>(moments(f[j]), gx[k][j], gy[k][j], c, u, v), fs);
+#pragma unroll
+            for (int p = 0; p < 8; ++p) s[p * PL + 32 * j] = fs[p];
+        }
+    }
+    __syncthreads();
+    // Step 2: f*(t+2) of the slots one node inside the edge, from A into B.
+#pragma unroll
+    for (int k = 0; k < kT3Rows; ++k) {
+        const int r = warp + 8 * k;
+        if (r < 1 || r > kT3H - 2) continue;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int col = lane + 32 * j;
+            if (col < 1 || col > kT3W - 2) continue;
+            const float* s = smA + r * kT3W + col;
+            float f[8];
+            f[0] = s[0 * PL - 1];               // f_p(x) = f*_p(x - c_p)
+            f[1] = s[1 * PL - kT3W];
+            f[2] = s[2 * PL + 1];
+            f[3] = s[3 * PL + kT3W];
+            f[4] = s[4 * PL - kT3W - 1];
+            f[5] = s[5 * PL - kT3W + 1];
+            f[6] = s[6 * PL + kT3W + 1];
+            f[7] = s[7 * PL + kT3W - 1];
+            float u, v, fs[8];
+            populations(collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), fs);
+            float* d = smB + r * kT3W + col;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
+        }
+    }
+    float* __restrict__ snap = static_cast<float*>(a.snap);
+    const int64_t n = (int64_t)nx * ny;
+    float so[kT3Rows][2][2];
+    if (CHECK) {
+#pragma unroll
+        for (int k = 0; k < kT3Rows; ++k) {
+            const int r = warp + 8 * k, y = y0 + r;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int col = lane + 32 * j, x = x0 + col;
+                so[k][j][0] = so[k][j][1] = 0.0f;
+                if (r >= 2 && r <= kT3H - 3 && y < ny && col >= 2 && col <= kT3W - 3 && x < nx) {
+                    so[k][j][0] = snap[(int64_t)y * nx + x];
+                    so[k][j][1] = snap[n + (int64_t)y * nx + x];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // Step 3: the tile's nodes pull f*(t+2) from B and store f*(t+3).
+#pragma unroll
+    for (int k = 0; k < kT3Rows; ++k) {
+        const int r = warp + 8 * k;
+        const int y = y0 + r;
+        if (r < 2 || r > kT3H - 3 || y >= ny) continue;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int col = lane + 32 * j;
+            const int x = x0 + col;
+            if (col < 2 || col > kT3W - 3 || x >= nx) continue;
+            const int64_t idx = (int64_t)y * nx + x;
+            const float* s = smB + r * kT3W + col;
+            float f[8];
+            f[0] = s[0 * PL - 1];
+            f[1] = s[1 * PL - kT3W];
+            f[2] = s[2 * PL + 1];
+            f[3] = s[3 * PL + kT3W];
+            f[4] = s[4 * PL - kT3W - 1];
+            f[5] = s[5 * PL - kT3W + 1];
+            f[6] = s[6 * PL + kT3W + 1];
+            f[7] = s[7 * PL + kT3W - 1];
+            float u, v;
+            scatter_local<S>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
+            if (CHECK) {
+                snap[idx] = u;
+                snap[n + idx] = v;
+                const float du = u - so[k][j][0], dv = v - so[k][j][1];
+                acc[0] = fmaxf(acc[0], fmaxf(fabsf(du), fabsf(dv)));
+                acc[1] = fmaxf(acc[1], fmaxf(fabsf(u), fabsf(v)));
+                acc[2] += du * du + dv * dv;
+                acc[3] += u * u + v * v;
+                if (!(isfinite(u) && isfinite(v))) acc[4] = 1.0f;
+            }
+        }
+    }
+}
+
+template <int S, bool GEN, bool CHECK, bool ANY>
+__global__ void __launch_bounds__(kT2Threads, LBM_MINB_T3)
+k_step3(const StepParams a, const Coef<float> c) {
+    extern __shared__ float t3_smem[];
+    const int ntx = (a.nx + kT3OX - 1) / kT3OX;
+    const int64_t ntiles = (int64_t)ntx * ((a.ny + kT3OY - 1) / kT3OY);
+    float acc[kRes] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
+        step3_tile<S, GEN, CHECK, ANY>(a, c, t3_smem, tx, ty, acc);
         if (t + gridDim.x < ntiles) __syncthreads();   // slots are reused by the next tile
     }
     if (CHECK) residual_reduce<float>(a, acc);
@@ -717,7 +887,7 @@ inline int64_t step_tiles(int nx, int ny, int V) {
 }
 
 // Grid cap of the residual-check launches: one FP64 partial set per block.
-constexpr int64_t kMaxCheckBlocks = int64_t(1) << 18;
+constexpr int64_t kMaxCheckBlocks = int64_t(1) << 19;
 
 // Two-step launches of a single lattice: from one full slot array up (smaller
 // lattices would mostly compute duplicate slots).
@@ -726,6 +896,19 @@ inline bool step2_fits(int nx, int ny) { return nx >= kT2W && ny >= kT2H; }
 inline int64_t step2_tiles(int nx, int ny) {
     return (int64_t)((nx + kT2OX - 1) / kT2OX) * ((ny + kT2OY - 1) / kT2OY);
 }
+
+// Three-step launches of a single lattice: from one full slot array up.
+inline bool step3_fits(int nx, int ny) { return nx >= kT3W && ny >= kT3H; }
+
+inline int64_t step3_tiles(int nx, int ny) {
+    return (int64_t)((nx + kT3OX - 1) / kT3OX) * ((ny + kT3OY - 1) / kT3OY);
+}
+
+// Three fused steps (k_step3); defined with each storage type's kernels.
+cudaError_t step3_f32(const StepParams& a, const Coef<float>& c, bool gen, bool check,
+                      int check_blocks, cudaStream_t st);
+cudaError_t step3_f16s(const StepParams& a, const Coef<float>& c, bool gen, bool check,
+                       int check_blocks, cudaStream_t st);
 
 // Two fused steps (k_step2) of FP32 or FP16-shifted storage; defined with
 // each storage type's kernels.

@@ -19,33 +19,40 @@ def bench():
 
 
 def simulate_launches(iters, check_every, spl):
-    """Launch sequence of lbm_iterate_checked from step 0, written out step by
-    step: plain steps are paired when two steps run per launch, and a check
-    step (index + 1 a multiple of check_every) is the second of a pair."""
+    """Launch sequence of lbm_iterate_checked from step 0, written out launch
+    by launch as the library plans it: plain steps grouped into launches of spl
+    steps, leftovers in launches of 2 or 1, and a check step (index + 1 a
+    multiple of check_every) as the last step of a launch."""
+    def plain(m):
+        count = 0
+        while m > 0:
+            k = min(spl, m)
+            if spl == 3 and m == 4:
+                k = 2          # 4 = 2 + 2 instead of 3 + 1
+            m -= k
+            count += 1
+        return count
     launches, step, left = 0, 0, iters
     while left > 0:
         to_check = check_every - step % check_every
         if to_check > left:
-            plain = left
-            launches += (plain // 2 + plain % 2) if spl == 2 else plain
+            launches += plain(left)
             break
-        if spl == 2 and to_check >= 2:
-            plain = to_check - 2
-            launches += plain // 2 + plain % 2 + 1
-        else:
-            launches += to_check
+        last = min(spl, to_check)
+        launches += plain(to_check - last) + 1
         step += to_check
         left -= to_check
     return launches
 
 
-@pytest.mark.parametrize("spl", [1, 2])
+@pytest.mark.parametrize("spl", [1, 2, 3])
 def test_launch_count_matches_the_schedule(bench, spl):
     for iters in (0, 1, 2, 7, 99, 100, 101, 1000, 1234):
         for ce in (1, 2, 3, 7, 10, 100):
             assert bench.launches_per_iterate(iters, ce, spl) == simulate_launches(iters, ce, spl), (iters, ce)
     assert bench.launches_per_iterate(1000, 100, 2) == 500
     assert bench.launches_per_iterate(1000, 100, 1) == 1000
+    assert bench.launches_per_iterate(1000, 100, 3) == 10 * (33 + 1)   # 97 = 31 x 3 + 2 + 2
 
 
 def test_kernel_hash_ignores_comments_but_not_code(bench, tmp_path):

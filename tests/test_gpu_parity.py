@@ -276,19 +276,19 @@ def test_f16s_force_rescale_keeps_state():
 @pytest.mark.parametrize("dtype", ["f32", "f16s"])
 def test_full_size_sampled_parity(dtype):
     """16384 x 16384 (the throughput workload) in the benchmark's launch
-    configuration (FP32: two steps per launch, plain and checked): after 4
-    steps from the zero state every node depends on the force within 4 nodes, so sampled nodes are checked one by one against
+    configuration (three steps per launch, plain and checked): after 6 steps
+    from the zero state every node depends on the force within 6 nodes, so sampled nodes are checked one by one against
     the oracle run on a small periodic window around each sample."""
     n = 16384
-    steps = 4
+    steps = 6
     lam, mu = W.lame_2d(1.0, 0.3)
     rates = oracle.relaxation_rates(lam, mu)
     pw = W.random_force(n, n, 16, 8, seed=0x16384)
     gx, gy = W.random_force_grid(pw)
     with Lattice(n, n, lam, mu, dtype) as lat:
         lat.set_force(gx, gy)
-        lat.iterate(2)                  # FP32: one plain two-step launch
-        lat.iterate_checked(2, 2)       # and one two-step check launch
+        lat.iterate(3)                  # one plain three-step launch
+        lat.iterate_checked(3, 3)       # and one three-step check launch
         out = torch.empty(5 * n * n, dtype=torch.float64, device="cuda")
         lat.fields_device(out)
         got = out.view(5, n, n)

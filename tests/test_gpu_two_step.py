@@ -29,7 +29,7 @@ def _pair(nx, ny, seed=1, **kw):
     for lat in (a, b):
         lat.set_force(gx, gy)
     a.steps_per_launch = 1
-    assert b.steps_per_launch == 2
+    b.steps_per_launch = 2
     return a, b, gx, gy, lam, mu
 
 
@@ -86,7 +86,7 @@ def test_two_step_matches_oracle():
     gx, gy = W.random_force_grid(pw)
     ref = oracle.run(oracle.zero_state(nx, ny), gx, gy, rates, 6)
     with Lattice(nx, ny, lam, mu, "f32") as lat:
-        assert lat.steps_per_launch == 2
+        lat.steps_per_launch = 2
         lat.set_force(gx, gy)
         lat.iterate(6)
         got, want = lat.fields(), oracle.fields(ref, gx, gy, rates)
@@ -96,22 +96,25 @@ def test_two_step_matches_oracle():
 
 
 def test_steps_per_launch_availability():
-    """Default: two steps from 64 x 24 on for FP32 and FP16S; any FP32/FP16S
-    lattice may choose two; FP64 always one."""
+    """Default: three steps from 64 x 16 on for FP32 and FP16S; any FP32/FP16S
+    lattice may choose one to three; FP64 always one."""
     lam, mu = W.lame_2d(1.0, 0.3)
-    for nx, ny, dt, want in ((64, 24, "f32", 2), (63, 32, "f32", 1), (64, 23, "f32", 1),
-                             (256, 256, "f64", 1), (256, 256, "f16s", 2), (63, 64, "f16s", 1)):
+    for nx, ny, dt, want in ((64, 16, "f32", 3), (63, 32, "f32", 1), (64, 15, "f32", 1),
+                             (256, 256, "f64", 1), (256, 256, "f16s", 3), (63, 64, "f16s", 1)):
         with Lattice(nx, ny, lam, mu, dt) as lat:
             assert lat.steps_per_launch == want, (nx, ny, dt)
             lat.steps_per_launch = 1
             if dt == "f64":
-                with pytest.raises(P.LBMError):
-                    lat.steps_per_launch = 2
+                for k in (2, 3):
+                    with pytest.raises(P.LBMError):
+                        lat.steps_per_launch = k
             else:
-                lat.steps_per_launch = 2
-                assert lat.steps_per_launch == 2
-            with pytest.raises(P.LBMError):
-                lat.steps_per_launch = 3
+                for k in (2, 3):
+                    lat.steps_per_launch = k
+                    assert lat.steps_per_launch == k
+            for k in (0, 4):
+                with pytest.raises(P.LBMError):
+                    lat.steps_per_launch = k
 
 
 # Lattices smaller than the 64 x 24 slot array appear in it more than once
@@ -164,9 +167,66 @@ def test_two_step_f16s_conserves_mean_displacement():
     pw = W.random_force(nx, ny, 8, 4, seed=8)
     gx, gy = W.random_force_grid(pw)
     with Lattice(nx, ny, lam, mu, "f16s") as lat:
-        assert lat.steps_per_launch == 2
+        assert lat.steps_per_launch == 3
         lat.set_force(gx, gy)
         lat.iterate(2000)
         u = lat.displacement()
         scale = float(np.max(np.abs(u)))
         assert abs(float(np.mean(u[0]))) < 1e-4 * scale and abs(float(np.mean(u[1]))) < 1e-4 * scale
+
+
+# Three steps per launch: tile 60 x 12 nodes, slot arrays 64 x 16.
+@pytest.mark.parametrize("nx,ny", [(64, 16), (130, 70), (517, 33), (64, 300), (1, 1), (5, 5), (63, 15), (7, 130)])
+@pytest.mark.parametrize("steps", [1, 2, 3, 7, 11])
+def test_three_step_launch_is_bit_identical(nx, ny, steps):
+    lam, mu = W.lame_2d(1.0, 0.3)
+    pw = W.random_force(nx, ny, 8, 4, seed=31)
+    gx, gy = W.random_force_grid(pw)
+    out = []
+    for spl in (1, 3):
+        with Lattice(nx, ny, lam, mu, "f32") as lat:
+            lat.steps_per_launch = spl
+            lat.set_force(gx, gy)
+            lat.iterate(steps)
+            assert lat.step == steps
+            out.append(lat.populations())
+    assert np.array_equal(out[0], out[1]), float(np.max(np.abs(out[0] - out[1])))
+
+
+@pytest.mark.parametrize("check_every", [2, 3, 7, 10])
+def test_three_step_checked_windows_and_solve(check_every):
+    lam, mu = W.lame_2d(1.0, 0.3)
+    nx, ny = 128, 96
+    pw = W.random_force(nx, ny, 8, 4, seed=32)
+    gx, gy = W.random_force_grid(pw)
+    res = []
+    for spl in (1, 3):
+        with Lattice(nx, ny, lam, mu, "f32", tau12=0.9, tau22=0.3) as lat:
+            lat.steps_per_launch = spl
+            lat.set_force(gx, gy)
+            r = lat.iterate_checked(41, check_every)
+            s = lat.solve(1e-6, 200000, 100)
+            res.append((lat.populations(), r, s))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1][0] == res[1][1][0] and res[0][1][2] == res[1][1][2]
+    assert res[0][2] == res[1][2]
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 16), (130, 70)])
+def test_three_step_f16s_matches_single_step_and_oracle(nx, ny):
+    lam, mu = W.lame_2d(1.0, 0.3)
+    rates = oracle.relaxation_rates(lam, mu)
+    pw = W.random_force(nx, ny, 8, 4, seed=33)
+    gx, gy = W.random_force_grid(pw)
+    steps = 42
+    ref = oracle.fields(oracle.run(oracle.zero_state(nx, ny), gx, gy, rates, steps), gx, gy, rates)
+    out = {}
+    for spl in (1, 3):
+        with Lattice(nx, ny, lam, mu, "f16s") as lat:
+            lat.steps_per_launch = spl
+            lat.set_force(gx, gy)
+            lat.iterate_checked(steps, 7)
+            out[spl] = lat.fields()
+    e1, e3, d = _rel(out[1], ref), _rel(out[3], ref), _rel(out[3], out[1])
+    print("f16s one step/launch %.2e, three %.2e, between %.2e" % (e1, e3, d))
+    assert e1 < 2e-3 and e3 < 2e-3 and d < 2e-3
