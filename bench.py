@@ -281,7 +281,7 @@ def launches_per_iterate(iters, check_every, spl):
     """Stream-collide launches of lbm_iterate_checked(iters, check_every) from
     step 0: each window is check_every - 1 plain steps grouped into launches of
     spl steps (the remainder in shorter ones) and ends with the check step,
-    the last step of a launch of min(spl, check_every) steps."""
+    the last step of a launch of min(spl, 2, check_every) steps."""
     def plain(m):
         if spl == 3:
             if m % 3 == 1 and m >= 4:
@@ -292,7 +292,7 @@ def launches_per_iterate(iters, check_every, spl):
         return m
 
     def window(w):
-        last = min(spl, w)
+        last = min(spl, 2, w)       # checks ride on launches of at most two steps
         return plain(w - last) + 1
     total, left = 0, iters
     while left >= check_every:
@@ -374,7 +374,7 @@ def dominant_block(check_every, spl):
     """Steps at the start of a residual window that the library runs as whole
     plain launches of spl steps (lbm_iterate_checked plans the window's
     check_every - 1 plain steps so; see launches_per_iterate)."""
-    m = check_every - min(spl, check_every)
+    m = check_every - min(spl, 2, check_every)
     if spl == 3:
         return 3 * ((m - 4) // 3 if m % 3 == 1 and m >= 4 else m // 3)
     if spl == 2:

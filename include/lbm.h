@@ -121,8 +121,8 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
  * streaming): the intermediate post-collision states of a tile and its halo
  * (one node per extra step) stay on chip in FP32, so the populations cross
  * device memory once per k steps.  A residual check (lbm_iterate_checked,
- * lbm_solve) falls on the last step of a launch; steps left over when n is not
- * a multiple of k run in shorter launches.  With LBM_F32 storage the
+ * lbm_solve) falls on the last step of a launch of at most two steps; steps
+ * left over when n is not a multiple of k run in shorter launches.  With LBM_F32 storage the
  * arithmetic per node is unchanged and the state after every launch equals
  * that of the same steps taken one per launch, bit for bit.  With LBM_F16S
  * storage the intermediate states are not rounded to the FP16 storage format,

@@ -77,7 +77,6 @@ struct lbm_ctx {
     int64_t nblocks = 0;           // grid of the residual-check launch
     int spl = 1;                   // pseudo-time steps per stream-collide launch (1, 2 or 3)
     int64_t nblocks2 = 0;          // grid of the two-step check launch
-    int64_t nblocks3 = 0;          // grid of the three-step check launch
 };
 
 namespace {
@@ -166,14 +165,12 @@ cudaError_t launch_step2(lbm_ctx* c, bool check) {
     return e;
 }
 
-// Three steps in one launch (FP32 or FP16-shifted storage); with check the
-// third step is the residual-check step.
-cudaError_t launch_step3(lbm_ctx* c, bool check) {
+// Three plain steps in one launch (FP32 or FP16-shifted storage).
+cudaError_t launch_step3(lbm_ctx* c) {
     const StepParams a = params(c, c->cur);
     cudaError_t e = c->dtype == LBM_F32
-                        ? step3_f32(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks3, c->stream)
-                        : step3_f16s(a, coef<float>(c->rates), c->gen, check, (int)c->nblocks3, c->stream);
-    if (e == cudaSuccess && check) e = finish_residual_launch(c, c->nblocks3);
+                        ? step3_f32(a, coef<float>(c->rates), c->gen, false, 0, c->stream)
+                        : step3_f16s(a, coef<float>(c->rates), c->gen, false, 0, c->stream);
     if (e == cudaSuccess) {
         c->cur ^= 1;
         c->step += 3;
@@ -189,7 +186,7 @@ cudaError_t run_plain(lbm_ctx* c, int64_t n) {
     cudaError_t e = cudaSuccess;
     if (c->spl == 3) {
         const int64_t triples = n % 3 == 1 && n >= 4 ? (n - 4) / 3 : n / 3;
-        for (int64_t i = 0; i < triples && e == cudaSuccess; ++i) e = launch_step3(c, false);
+        for (int64_t i = 0; i < triples && e == cudaSuccess; ++i) e = launch_step3(c);
         n -= 3 * triples;
     }
     if (c->spl >= 2)
@@ -199,13 +196,11 @@ cudaError_t run_plain(lbm_ctx* c, int64_t n) {
 }
 
 // to_check - 1 plain steps followed by the residual-check step (the last
-// step of the last launch).
+// step of the last launch).  With three steps per launch the check still
+// rides on a two-step launch: a three-step launch with the check costs twice
+// a plain one, a two-step launch with the check 1.3 times.
 cudaError_t run_window(lbm_ctx* c, int64_t to_check) {
     cudaError_t e;
-    if (c->spl == 3 && to_check >= 3) {
-        e = run_plain(c, to_check - 3);
-        return e == cudaSuccess ? launch_step3(c, true) : e;
-    }
     if (c->spl >= 2 && to_check >= 2) {
         e = run_plain(c, to_check - 2);
         return e == cudaSuccess ? launch_step2(c, true) : e;
@@ -423,7 +418,6 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     c->nblocks = std::min(step_tiles(nx, ny, c->V), kMaxCheckBlocks);
     if (dtype != LBM_F64) {
         c->nblocks2 = std::min(step2_tiles(nx, ny), kMaxCheckBlocks);
-        c->nblocks3 = std::min(step3_tiles(nx, ny), kMaxCheckBlocks);
         if (step3_fits(nx, ny)) c->spl = 3;
         else if (step2_fits(nx, ny)) c->spl = 2;
     }
@@ -445,7 +439,7 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     const size_t snap_bytes = (dtype == LBM_F64 ? sizeof(double) : sizeof(float)) * 2 * c->n;
     if (e == cudaSuccess) e = alloc(&c->snap, snap_bytes);
     if (e == cudaSuccess) e = alloc((void**)&c->partials,
-                                       sizeof(double) * kRes * std::max(c->nblocks, std::max(c->nblocks2, c->nblocks3)));
+                                       sizeof(double) * kRes * std::max(c->nblocks, c->nblocks2));
     if (e == cudaSuccess) e = alloc((void**)&c->result, sizeof(double) * kRes);
     if (e == cudaSuccess) e = alloc((void**)&c->absmax, sizeof(unsigned long long));
     if (e == cudaSuccess) e = alloc((void**)&c->bad, sizeof(unsigned int));

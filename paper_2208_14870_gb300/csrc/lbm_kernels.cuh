@@ -572,8 +572,10 @@ k_step2(const StepParams a, const Coef<float> c) {
 // slot columns lane and lane + 32 and rows warp + 8k in all three steps; the
 // per-node arithmetic is the single step's, so FP32 results equal three
 // single-step launches bit for bit (FP16S keeps the two intermediate states
-// in FP32).  CHECK makes the third step the residual-check step.  ANY as for
-// k_step2; the library uses the ANY = false kernel from kT3W x kT3H nodes up.
+// in FP32).  CHECK would make the third step the residual-check step; the
+// library puts its checks on two-step launches instead, which cost less
+// relative to their plain form.  ANY as for k_step2; the library uses the
+// ANY = false kernel from kT3W x kT3H nodes up.
 #ifndef LBM_T3_RPW
 #define LBM_T3_RPW 2
 #endif

@@ -46,39 +46,30 @@ static cudaError_t t3_allow_smem() {
     if (done[dev]) return cudaSuccess;
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
     e = cudaFuncSetAttribute(k_step3<S, false, false, false>, at, kT3Smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<S, false, true, false>, at, kT3Smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<S, true, false, false>, at, kT3Smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<S, true, true, false>, at, kT3Smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<S, false, false, true>, at, kT3Smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<S, false, true, true>, at, kT3Smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<S, true, false, true>, at, kT3Smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<S, true, true, true>, at, kT3Smem);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
-// Three fused steps: one block per tile (check: up to check_blocks blocks).
+// Three fused plain steps, one block per tile.  (The library puts residual
+// checks on two-step launches; a checked three-step launch is not offered.)
 template <int S>
 static cudaError_t launch_step3(const StepParams& a, const Coef<float>& c, bool gen, bool check,
                                 int check_blocks, cudaStream_t st) {
+    (void)check_blocks;
+    if (check) return cudaErrorNotSupported;
     cudaError_t e = t3_allow_smem<S>();
     if (e != cudaSuccess) return e;
-    const int64_t tiles = step3_tiles(a.nx, a.ny);
-    const unsigned int grid = (unsigned int)(check ? (tiles < check_blocks ? tiles : check_blocks) : tiles);
+    const unsigned int grid = (unsigned int)step3_tiles(a.nx, a.ny);
     const dim3 block(kT2Threads);
-    if (!step3_fits(a.nx, a.ny)) {   // lattice smaller than the slot array
-        if (gen) {
-            if (check) k_step3<S, true, true, true><<<grid, block, kT3Smem, st>>>(a, c);
-            else k_step3<S, true, false, true><<<grid, block, kT3Smem, st>>>(a, c);
-        } else {
-            if (check) k_step3<S, false, true, true><<<grid, block, kT3Smem, st>>>(a, c);
-            else k_step3<S, false, false, true><<<grid, block, kT3Smem, st>>>(a, c);
-        }
-    } else if (gen) {
-        if (check) k_step3<S, true, true, false><<<grid, block, kT3Smem, st>>>(a, c);
-        else k_step3<S, true, false, false><<<grid, block, kT3Smem, st>>>(a, c);
+    const bool any = !step3_fits(a.nx, a.ny);   // lattice smaller than the slot array
+    if (any) {
+        if (gen) k_step3<S, true, false, true><<<grid, block, kT3Smem, st>>>(a, c);
+        else k_step3<S, false, false, true><<<grid, block, kT3Smem, st>>>(a, c);
     } else {
-        if (check) k_step3<S, false, true, false><<<grid, block, kT3Smem, st>>>(a, c);
+        if (gen) k_step3<S, true, false, false><<<grid, block, kT3Smem, st>>>(a, c);
         else k_step3<S, false, false, false><<<grid, block, kT3Smem, st>>>(a, c);
     }
     return cudaGetLastError();

@@ -22,7 +22,8 @@ def simulate_launches(iters, check_every, spl):
     """Launch sequence of lbm_iterate_checked from step 0, written out launch
     by launch as the library plans it: plain steps grouped into launches of spl
     steps, leftovers in launches of 2 or 1, and a check step (index + 1 a
-    multiple of check_every) as the last step of a launch."""
+    multiple of check_every) as the last step of a launch of at most two
+    steps."""
     def plain(m):
         count = 0
         while m > 0:
@@ -38,7 +39,7 @@ def simulate_launches(iters, check_every, spl):
         if to_check > left:
             launches += plain(left)
             break
-        last = min(spl, to_check)
+        last = min(spl, 2, to_check)      # the check rides on a launch of at most two steps
         launches += plain(to_check - last) + 1
         step += to_check
         left -= to_check
@@ -52,7 +53,7 @@ def test_launch_count_matches_the_schedule(bench, spl):
             assert bench.launches_per_iterate(iters, ce, spl) == simulate_launches(iters, ce, spl), (iters, ce)
     assert bench.launches_per_iterate(1000, 100, 2) == 500
     assert bench.launches_per_iterate(1000, 100, 1) == 1000
-    assert bench.launches_per_iterate(1000, 100, 3) == 10 * (33 + 1)   # 97 = 31 x 3 + 2 + 2
+    assert bench.launches_per_iterate(1000, 100, 3) == 10 * (33 + 1)   # 98 = 32 x 3 + 2, then the check pair
 
 
 def test_kernel_hash_ignores_comments_but_not_code(bench, tmp_path):
