@@ -59,10 +59,10 @@ FP64_PEAK_GINST = 625.0
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
-    "f32_x3": {"bytes_per_launch": (673.154560e6 + 495.588608e6) * 16, "kernel_hash": "0b06d567794ba4bf",
-               "ncu": {"dram_throughput_pct": 58.4, "issue_active_pct": 62.5, "top_stall": "not_selected"}},
-    "f16s_x3": {"bytes_per_launch": (538.734080e6 + 367.194112e6) * 16, "kernel_hash": "0b06d567794ba4bf",
-                "ncu": {"dram_throughput_pct": 40.0, "issue_active_pct": 76.9, "top_stall": "not_selected"}},
+    "f32_x3": {"bytes_per_launch": (673.150976e6 + 498.287616e6) * 16, "kernel_hash": "72ac5d7b008eb4b5",
+               "ncu": {"dram_throughput_pct": 58.9, "issue_active_pct": 62.9, "top_stall": "not_selected"}},
+    "f16s_x3": {"bytes_per_launch": (538.608128e6 + 366.969344e6) * 16, "kernel_hash": "72ac5d7b008eb4b5",
+                "ncu": {"dram_throughput_pct": 40.1, "issue_active_pct": 77.2, "top_stall": "not_selected"}},
     "f32_x2": {"bytes_per_launch": (674.853888e6 + 493.407488e6) * 16, "kernel_hash": "357960238ea21163"},
     "f32_x1": {"bytes_per_launch": (671.173632e6 + 485.997824e6) * 16, "kernel_hash": "357960238ea21163"},
     "f16s_x1": {"bytes_per_launch": (536.988928e6 + 367.846144e6) * 16, "kernel_hash": "357960238ea21163"},
