@@ -42,6 +42,8 @@ FALLBACK_HBM_GBS = 6800.0
 # written + 2 force components read; FP16-shifted adds the two FP32
 # first-moment carriers read and written.  A launch advances one step, or two
 # (FP32 two-step kernel): bytes per lattice update = this / steps per launch.
+# the wavefront kernel runs from this lattice width up (one strip of slots)
+WAVE_MIN_NX = 256
 BYTES_PER_LAUNCH_NODE = {"f64": 8 * 8 * 2 + 2 * 8, "f32": 8 * 4 * 2 + 2 * 4, "f16s": (8 * 2 + 2 * 4) * 2 + 2 * 4}
 FORCE_SEED = 0x2208_14870
 # FP64 storage runs its collision on the FP64 pipe: 42 FP64 instructions per
@@ -277,31 +279,45 @@ def host_description():
 # Our arm
 # ---------------------------------------------------------------------------
 
-def launches_per_iterate(iters, check_every, spl):
+def plan_plain(m, spl, wave=False):
+    """Launch sizes of m plain steps as the library groups them: launches of
+    spl steps (four only on the wavefront schedule, else three), a remainder
+    of one avoided where possible (4 = 2 + 2, 5 = 3 + 2), then pairs, then
+    single steps."""
+    sizes = []
+    big = 4 if spl >= 4 and wave else (3 if spl >= 3 else 0)
+    if big:
+        groups, r = divmod(m, big)
+        if r == 1 and groups >= 1:
+            groups, r = groups - 1, r + big
+        sizes += [big] * groups
+        m = r
+        if big == 4 and m >= 3:
+            sizes.append(3)
+            m -= 3
+    if spl >= 2:
+        sizes += [2] * (m // 2)
+        m %= 2
+    return sizes + [1] * m
+
+
+def launches_per_iterate(iters, check_every, spl, wave=False):
     """Stream-collide launches of lbm_iterate_checked(iters, check_every) from
     step 0: each window is check_every - 1 plain steps grouped into launches of
     spl steps (the remainder in shorter ones) and ends with the check step,
     the last step of a launch of min(spl, 2, check_every) steps."""
-    def plain(m):
-        if spl == 3:
-            if m % 3 == 1 and m >= 4:
-                return (m - 4) // 3 + 2
-            return m // 3 + (1 if m % 3 else 0)
-        if spl == 2:
-            return m // 2 + m % 2
-        return m
-
     def window(w):
         last = min(spl, 2, w)       # checks ride on launches of at most two steps
-        return plain(w - last) + 1
+        return len(plan_plain(w - last, spl, wave)) + 1
     total, left = 0, iters
     while left >= check_every:
         total += window(check_every)
         left -= check_every
-    return total + plain(left)
+    return total + len(plan_plain(left, spl, wave))
 
 
-def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, spl=None, iters=None):
+def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, spl=None, iters=None,
+                 wave=None):
     """Device-resident timing of `nsteps` benchmark steps of `iters`
     pseudo-time steps each (default --iters); returns dict."""
     n = args.n
@@ -310,7 +326,10 @@ def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, 
     lat = P.Lattice(n, n, lam, mu, dtype)
     if spl is not None:
         lat.steps_per_launch = spl
+    if wave is not None and dtype != "f64":
+        lat.wavefront = wave
     spl = lat.steps_per_launch
+    wave_on = dtype != "f64" and lat.wavefront != 0 and n >= WAVE_MIN_NX
     stream = torch.cuda.current_stream()
     lat.set_stream(stream.cuda_stream)
     lat.set_force(gx_d, gy_d)
@@ -318,12 +337,12 @@ def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, 
 
     ce = args.check_every
     windows, rest = divmod(iters, ce)
-    block = dominant_block(ce, spl)
+    block, big = dominant_block(ce, spl, wave_on)
     nev = nsteps * windows
 
     def one_step(ev_a=None, ev_b=None, dom=None):
         # The same launches as lbm_iterate_checked(iters, check_every): per
-        # window, its whole launches of the dominant kernel (plain, spl steps
+        # window, its whole launches of the dominant kernel (plain, `big` steps
         # each) between two events, then the rest of the window with its
         # check; the library places checks by step index, so splitting the
         # call changes nothing.
@@ -360,26 +379,26 @@ def time_variant(args, dtype, gx_d, gy_d, torch, P, nsteps, nwarm, events=True, 
     total_ms = t_start.elapsed_time(t_end)
     iter_ms = sum(a.elapsed_time(b) for a, b in evs)
     dom_ms = sum(devs[2 * k].elapsed_time(devs[2 * k + 1]) for k in range(nev))
-    dom_launches = nev * (block // spl)
+    dom_launches = nev * (block // big)
     lat.close()
     del out5
-    per_iter = launches_per_iterate(iters, args.check_every, spl)
+    per_iter = launches_per_iterate(iters, args.check_every, spl, wave_on)
     checks = iters // args.check_every      # each adds one residual-finish launch
     return {"total_ms": total_ms, "iter_ms": iter_ms, "steps": nsteps, "spl": spl, "iters": iters,
             "step_launches": nsteps * per_iter, "launches": nsteps * (per_iter + checks + 1),
-            "dom_ms": dom_ms, "dom_launches": dom_launches}
+            "dom_ms": dom_ms, "dom_launches": dom_launches, "big": big, "wave": wave_on}
 
 
-def dominant_block(check_every, spl):
-    """Steps at the start of a residual window that the library runs as whole
-    plain launches of spl steps (lbm_iterate_checked plans the window's
-    check_every - 1 plain steps so; see launches_per_iterate)."""
-    m = check_every - min(spl, 2, check_every)
-    if spl == 3:
-        return 3 * ((m - 4) // 3 if m % 3 == 1 and m >= 4 else m // 3)
-    if spl == 2:
-        return 2 * (m // 2)
-    return m
+def dominant_block(check_every, spl, wave=False):
+    """(steps, k): the first steps of a residual window, which the library
+    runs as whole plain launches of k steps each, k the longest launch of the
+    window (lbm_iterate_checked plans the window's check_every - 1 plain steps
+    so; see plan_plain)."""
+    sizes = plan_plain(check_every - min(spl, 2, check_every), spl, wave)
+    if not sizes:
+        return 0, spl
+    big = sizes[0]
+    return big * sum(1 for k in sizes if k == big), big
 
 
 def run_ours(args, ws, rank, local):
@@ -406,13 +425,14 @@ def run_ours(args, ws, rank, local):
     sampler = ClockSampler(local if ws > 1 else torch.cuda.current_device())
     barrier()
     sampler.start()
-    res = time_variant(args, args.dtype, gx_d, gy_d, torch, P, args.steps, args.warmup, spl=args.spl)
+    res = time_variant(args, args.dtype, gx_d, gy_d, torch, P, args.steps, args.warmup, spl=args.spl,
+                       wave=args.wave)
     barrier()
     clocks = sampler.stop()
     total_ms, lups = replica_aggregate(dist if ws > 1 else None, res["total_ms"],
                                        float(n) * n * args.iters * args.steps, device="cuda")
     value = lups / (total_ms / 1e3) / 1e6
-    spl = res["spl"]
+    spl = res["big"]          # steps per launch of the dominant kernel
     # the dominant kernel: plain launches of spl steps, timed by events around
     # them inside the timed region
     per_launch_s = res["dom_ms"] / 1e3 / res["dom_launches"]
@@ -420,7 +440,7 @@ def run_ours(args, ws, rank, local):
     # whatever number of steps it advances
     bpl = BYTES_PER_LAUNCH_NODE[args.dtype] * n * n
     achieved = bpl / per_launch_s / 1e9
-    tr = NCU_TRAFFIC.get("%s_x%d" % (args.dtype, spl))
+    tr = NCU_TRAFFIC.get("%s_x%d%s" % (args.dtype, spl, "w" if res["wave"] else ""))
     current = bool(tr) and tr.get("kernel_hash") == kernel_hash()
     traffic = tr["bytes_per_launch"] if current else None
     ncu_util = tr.get("ncu") if current else None
@@ -428,21 +448,24 @@ def run_ours(args, ws, rank, local):
     variants = {}
     if not args.quick:
         for name in args.variants:
-            dt, _, k = name.partition("x")
-            if name == args.dtype or dt not in BYTES_PER_LAUNCH_NODE:
+            mt = re.fullmatch(r"(f64|f32|f16s)(?:x(\d))?(w?)", name)
+            if name == args.dtype or mt is None:
                 continue
+            dt, k, w = mt.groups()
+            # "w": wavefront schedule; an explicit k without it: tile schedule
             r = time_variant(args, dt, gx_d, gy_d, torch, P, max(2, args.steps // 2), 2,
                              spl=int(k) if k else None,
-                             iters=args.f64_iters if dt == "f64" else None)
+                             iters=args.f64_iters if dt == "f64" else None,
+                             wave=args.wave_rows if w else (0 if k else None))
             pl = r["dom_ms"] / 1e3 / r["dom_launches"]
             b = BYTES_PER_LAUNCH_NODE[dt] * n * n
             lups = float(n) * n * r["iters"] * r["steps"] / (r["total_ms"] / 1e3)
             variants[name] = {
                 "value": lups / 1e6, "unit": "MLUPS", "ms_per_step": r["total_ms"] / r["steps"],
                 "iters_per_step": r["iters"],
-                "steps_per_launch": r["spl"], "kernel_us": pl * 1e6,
+                "steps_per_launch": r["big"], "wavefront": r["wave"], "kernel_us": pl * 1e6,
                 "achieved_gbs": b / pl / 1e9, "frac_of_measured_hbm": b / pl / 1e9 / peak,
-                "bytes_per_lup": BYTES_PER_LAUNCH_NODE[dt] / r["spl"]}
+                "bytes_per_lup": BYTES_PER_LAUNCH_NODE[dt] / r["big"]}
             if dt == "f64":
                 # FP64 is bound by the FP64 pipe, not by HBM: FP64 instructions
                 # per second over the pipe's nominal instruction rate
@@ -472,10 +495,12 @@ def run_ours(args, ws, rank, local):
             "config": workload_config(args),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": {1: "k_step<%s> (fused stream-collide)",
+                         "kernel": ("k_wave<%s,%d> (%d fused stream-collide steps per launch, "
+                                    "wavefront schedule)" % (args.dtype, spl, spl)) if res["wave"] else
+                                   {1: "k_step<%s> (fused stream-collide)",
                                     2: "k_step2<%s> (two fused stream-collide steps per launch)",
                                     3: "k_step3<%s> (three fused stream-collide steps per launch)"}[spl]
-                         % args.dtype,
+                                   % args.dtype,
                          "kernel_us": per_launch_s * 1e6, "steps_per_launch": spl,
                          "bytes_per_launch_node": BYTES_PER_LAUNCH_NODE[args.dtype],
                          "bytes_per_lup": BYTES_PER_LAUNCH_NODE[args.dtype] / spl,
@@ -736,10 +761,17 @@ def main():
     ap.add_argument("--nu", type=float, default=0.3)
     ap.add_argument("--spl", type=int, default=None,
                     help="steps per stream-collide launch of the main line (default: the library's choice)")
+    ap.add_argument("--wave", type=int, default=None,
+                    help="wavefront segment rows of the main line (0: tile schedule, -1: automatic; "
+                         "default: the library's choice)")
+    ap.add_argument("--wave-rows", type=int, default=-1,
+                    help="wavefront segment rows of the variants with a 'w' suffix (-1: automatic)")
     ap.add_argument("--f64-iters", type=int, default=100,
                     help="pseudo-time steps per benchmark step of the FP64 variant")
-    ap.add_argument("--variants", nargs="*", default=["f16s", "f32x2", "f32x1", "f16sx2", "f16sx1", "f64"],
-                    help="extra storage variants; a suffix xK fixes K steps per launch")
+    ap.add_argument("--variants", nargs="*",
+                    default=["f16s", "f32x3w", "f32x3", "f32x2", "f32x1", "f16sx3", "f16sx1", "f64"],
+                    help="extra storage variants; a suffix xK fixes K steps per launch on the tile "
+                         "schedule, xKw on the wavefront schedule")
     ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)

@@ -116,11 +116,13 @@ void lbm_destroy(lbm_ctx *ctx);
  * all later work of this context.  The caller keeps ownership of the stream. */
 int lbm_set_stream(lbm_ctx *ctx, void *stream);
 
-/* Pseudo-time steps per stream-collide launch: 1, 2 or 3.  With k > 1, one
+/* Pseudo-time steps per stream-collide launch: 1 to 4.  With k > 1, one
  * launch runs k consecutive steps of Algorithm 1 (Sec. 3.3, Eqs. collision and
- * streaming): the intermediate post-collision states of a tile and its halo
- * (one node per extra step) stay on chip in FP32, so the populations cross
- * device memory once per k steps.  A residual check (lbm_iterate_checked,
+ * streaming): the intermediate post-collision states stay on chip in FP32, so
+ * the populations cross device memory once per k steps.  Up to three steps
+ * this runs on tiles (the tile and a halo of one node per extra step in shared
+ * memory); four steps need the wavefront schedule (lbm_set_wavefront), and
+ * without it k = 4 runs as k = 3.  A residual check (lbm_iterate_checked,
  * lbm_solve) falls on the last step of a launch of at most two steps; steps
  * left over when n is not a multiple of k run in shorter launches.  With LBM_F32 storage the
  * arithmetic per node is unchanged and the state after every launch equals
@@ -128,14 +130,33 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
  * storage the intermediate states are not rounded to the FP16 storage format,
  * so results differ from one step per launch by less than that format's
  * rounding (and lie closer to the FP64 result).  Available for LBM_F32 and
- * LBM_F16S storage on any lattice; the default is 3 from nx >= 64 and
- * ny >= 16 on (a smaller lattice fills the on-chip tile more than once and is
- * faster one step per launch).  LBM_F64 storage always runs one step per
+ * LBM_F16S storage on any lattice; the default is 4 (wavefront schedule) from
+ * nx >= 256 and ny >= 8 on, else 3 from nx >= 64 and ny >= 16 on (a smaller
+ * lattice fills the on-chip tile more than once and is faster one step per
+ * launch).  LBM_F64 storage always runs one step per
  * launch.  Paper: the scheme advances one step at a time; grouping steps into
  * launches is a schedule of the same steps, not part of the method.
- * Errors: LBM_ERR_ARG (k outside 1..3, or k > 1 with LBM_F64 storage). */
+ * Errors: LBM_ERR_ARG (k outside 1..4, or k > 1 with LBM_F64 storage). */
 int lbm_set_steps_per_launch(lbm_ctx *ctx, int k);
 int lbm_get_steps_per_launch(lbm_ctx *ctx, int *k);
+
+/* Wavefront schedule of launches of three or four steps (rows > 0: segments
+ * of `rows` rows; rows = -1: segments chosen per launch), or the tile schedule
+ * (rows = 0).  On the wavefront schedule a block owns a strip of 256 slot
+ * columns and a segment of lattice rows and walks down the segment one row per
+ * iteration at every step level at once, step j trailing step j - 1 by two
+ * rows, each level keeping four rows in shared memory: the halo is 2(k - 1)
+ * columns per strip instead of a ring of nodes around every tile.  Same steps
+ * and, for LBM_F32, the same bits as one step per launch (see
+ * lbm_set_steps_per_launch).  Used where nx >= 256 and ny >= 8; smaller
+ * lattices keep the tile schedule.  With rows = -1 a segment is 128 rows,
+ * halved (down to 16) while the grid would have fewer than four waves of
+ * resident blocks.  Default -1 for LBM_F32 and LBM_F16S storage, 0 for
+ * LBM_F64.
+ * Errors: LBM_ERR_ARG (rows outside -1..2^20, or rows != 0 with LBM_F64
+ * storage). */
+int lbm_set_wavefront(lbm_ctx *ctx, int rows);
+int lbm_get_wavefront(lbm_ctx *ctx, int *rows);
 
 /* Body force (constant in pseudo-time, Sec. 2.1).  gx, gy: host arrays of
  * nx*ny doubles (lattice units), copied.  The force must be finite; the

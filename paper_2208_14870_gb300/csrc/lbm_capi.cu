@@ -75,7 +75,11 @@ struct lbm_ctx {
     int V = 1;
     size_t bytes = 0;
     int64_t nblocks = 0;           // grid of the residual-check launch
-    int spl = 1;                   // pseudo-time steps per stream-collide launch (1, 2 or 3)
+    int spl = 1;                   // pseudo-time steps per stream-collide launch (1 to 4)
+    int wave = 0;                  // launches of three or four steps: 0 tile kernel, > 0 wavefront
+                                   // kernel with segments of this many rows per block, -1 wavefront
+                                   // with the segment chosen per launch (wave_seg)
+    int nsm = 0;                   // multiprocessors of the device
     int64_t nblocks2 = 0;          // grid of the two-step check launch
 };
 
@@ -179,15 +183,54 @@ cudaError_t launch_step3(lbm_ctx* c) {
     return e;
 }
 
-// n plain steps, grouped into launches of c->spl steps; with three steps per
-// launch a remainder of one step is avoided where possible (4 = 2 + 2), since
-// a pair of steps costs about as much as one step alone.
+// Segment rows of a wavefront launch of T steps: the set value, or (-1)
+// kWvSegDefault halved, down to 16, while the grid would have fewer than four
+// waves of resident blocks (short segments cost 2(T - j) extra rows at level j).
+int wave_seg(const lbm_ctx* c, int T) {
+    if (c->wave > 0) return c->wave;
+    const int64_t want = 4LL * (c->nsm > 0 ? c->nsm : 1) * (T == 3 ? wv_minb<3>() : wv_minb<4>());
+    int seg = kWvSegDefault;
+    while (seg > 16 && (T == 3 ? wave_blocks<3>(c->nx, c->ny, seg) : wave_blocks<4>(c->nx, c->ny, seg)) < want)
+        seg /= 2;
+    return seg;
+}
+
+// T = 3 or 4 plain steps in one launch: the wavefront kernel where it is on
+// and fits, else (T = 3) the three-step tile kernel.
+cudaError_t launch_multi(lbm_ctx* c, int T) {
+    if (!(c->wave != 0 && wave_fits(c->nx, c->ny))) return T == 3 ? launch_step3(c) : cudaErrorInvalidValue;
+    const StepParams a = params(c, c->cur);
+    const int seg = wave_seg(c, T);
+    cudaError_t e = c->dtype == LBM_F32 ? wave_f32(a, coef<float>(c->rates), c->gen, T, seg, c->stream)
+                                        : wave_f16s(a, coef<float>(c->rates), c->gen, T, seg, c->stream);
+    if (e == cudaSuccess) {
+        c->cur ^= 1;
+        c->step += T;
+        c->staged_fields = false;
+    }
+    return e;
+}
+
+// n plain steps, grouped into launches of c->spl steps (four only on the
+// wavefront schedule, else three); a remainder of one step is avoided where
+// possible (4 = 2 + 2, 5 = 3 + 2), since a pair of steps costs about as much
+// as one step alone.
 cudaError_t run_plain(lbm_ctx* c, int64_t n) {
     cudaError_t e = cudaSuccess;
-    if (c->spl == 3) {
-        const int64_t triples = n % 3 == 1 && n >= 4 ? (n - 4) / 3 : n / 3;
-        for (int64_t i = 0; i < triples && e == cudaSuccess; ++i) e = launch_step3(c);
-        n -= 3 * triples;
+    const bool wave = c->wave != 0 && wave_fits(c->nx, c->ny);
+    const int big = c->spl >= 4 && wave ? 4 : (c->spl >= 3 ? 3 : 0);
+    if (big) {
+        int64_t groups = n / big, r = n % big;
+        if (r == 1 && groups >= 1) {
+            --groups;
+            r += big;
+        }
+        for (int64_t i = 0; i < groups && e == cudaSuccess; ++i) e = launch_multi(c, big);
+        n = r;
+        if (big == 4 && n >= 3 && e == cudaSuccess) {
+            e = launch_multi(c, 3);
+            n -= 3;
+        }
     }
     if (c->spl >= 2)
         for (; n >= 2 && e == cudaSuccess; n -= 2) e = launch_step2(c, false);
@@ -388,6 +431,7 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(LBM_ERR_OOM, "lbm_create: host allocation failed");
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {
         delete c;
         return cuda_fail(e, "cudaGetDevice");
@@ -418,7 +462,11 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
     c->nblocks = std::min(step_tiles(nx, ny, c->V), kMaxCheckBlocks);
     if (dtype != LBM_F64) {
         c->nblocks2 = std::min(step2_tiles(nx, ny), kMaxCheckBlocks);
-        if (step3_fits(nx, ny)) c->spl = 3;
+        // four steps per launch on the wavefront schedule where it fits, else
+        // three or two on tiles
+        c->wave = -1;
+        if (wave_fits(nx, ny)) c->spl = 4;
+        else if (step3_fits(nx, ny)) c->spl = 3;
         else if (step2_fits(nx, ny)) c->spl = 2;
     }
 
@@ -478,7 +526,7 @@ void lbm_destroy(lbm_ctx* c) {
 int lbm_set_steps_per_launch(lbm_ctx* c, int k) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if (k < 1 || k > 3) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: k must be 1, 2 or 3");
+    if (k < 1 || k > 4) return fail(LBM_ERR_ARG, "lbm_set_steps_per_launch: k must be 1, 2, 3 or 4");
     if (k > 1 && c->dtype == LBM_F64)
         return fail(LBM_ERR_ARG,
                     "lbm_set_steps_per_launch: several steps per launch need FP32 or FP16-shifted storage");
@@ -491,6 +539,25 @@ int lbm_get_steps_per_launch(lbm_ctx* c, int* k) {
     if (rc) return rc;
     if (!k) return fail(LBM_ERR_ARG, "lbm_get_steps_per_launch: null pointer");
     *k = c->spl;
+    return LBM_OK;
+}
+
+int lbm_set_wavefront(lbm_ctx* c, int rows) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (rows < -1 || rows > (1 << 20))
+        return fail(LBM_ERR_ARG, "lbm_set_wavefront: rows must be -1 (automatic), 0 (off) or in [1, 2^20]");
+    if (rows != 0 && c->dtype == LBM_F64)
+        return fail(LBM_ERR_ARG, "lbm_set_wavefront: the wavefront kernel needs FP32 or FP16-shifted storage");
+    c->wave = rows;
+    return LBM_OK;
+}
+
+int lbm_get_wavefront(lbm_ctx* c, int* rows) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!rows) return fail(LBM_ERR_ARG, "lbm_get_wavefront: null pointer");
+    *rows = c->wave;
     return LBM_OK;
 }
 

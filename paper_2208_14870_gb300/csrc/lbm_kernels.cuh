@@ -81,15 +81,17 @@ struct StepParams {
 
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
-__device__ __forceinline__ float ld_h(const __half* p) { return __half2float(__ldg(p)); }
 
-// Gather the pre-collision populations of node (x, y): f_p(x) = f*_p(x - c_p).
+// Stored values that the pull of one node reads: the 8 populations f*_p(x - c_p)
+// as stored (and, FP16S, the carriers of the 8 source nodes).
+template <int S> struct Pulled { typename StoreT<S>::P p[8]; };
+template <> struct Pulled<S_F16S> { __half p[8]; float2 c[8]; };
+
+// Load the stored values of the pull of node (x, y) (loads only).
 // r0, rm, rp: offsets of rows y, y-1, y+1 (wrapped); xm, xp: columns x-1, x+1.
 template <int S>
-__device__ __forceinline__ void gather(const StepParams& a, int64_t r0, int64_t rm, int64_t rp,
-                                       int x, int xm, int xp, typename StoreT<S>::T f[8],
-                                       typename StoreT<S>::T theta) {
-    using T = typename StoreT<S>::T;
+__device__ __forceinline__ void pull_load(const StepParams& a, int64_t r0, int64_t rm, int64_t rp,
+                                          int x, int xm, int xp, Pulled<S>& q) {
     using P = typename StoreT<S>::P;
     const P* s = static_cast<const P*>(a.src);
     const int64_t pl = a.plane;
@@ -97,31 +99,60 @@ __device__ __forceinline__ void gather(const StepParams& a, int64_t r0, int64_t 
     const int64_t i4 = rm + xm, i5 = rm + xp, i6 = rp + xp, i7 = rp + xm;
     if constexpr (S == S_F16S) {
         // carriers interleaved per node: (m*_10, m*_01) as one float2
-        const float hinv = a.hinv;
         const float2* c = reinterpret_cast<const float2*>(a.csrc);
-        const float k1 = 0.5f * (1.0f - theta), k5 = 0.25f * theta;
-        const float2 c0 = ldg(c + i0), c1 = ldg(c + i1), c2 = ldg(c + i2), c3 = ldg(c + i3);
-        const float2 c4 = ldg(c + i4), c5 = ldg(c + i5), c6 = ldg(c + i6), c7 = ldg(c + i7);
-        // (the FP16 value times the power-of-two 1/scale is exact)
-        f[0] = fmad(k1, c0.x, ld_h(s + 0 * pl + i0) * hinv);
-        f[1] = fmad(k1, c1.y, ld_h(s + 1 * pl + i1) * hinv);
-        f[2] = fmad(-k1, c2.x, ld_h(s + 2 * pl + i2) * hinv);
-        f[3] = fmad(-k1, c3.y, ld_h(s + 3 * pl + i3) * hinv);
-        f[4] = fmad(k5, c4.x + c4.y, ld_h(s + 4 * pl + i4) * hinv);
-        f[5] = fmad(k5, c5.y - c5.x, ld_h(s + 5 * pl + i5) * hinv);
-        f[6] = fmad(-k5, c6.x + c6.y, ld_h(s + 6 * pl + i6) * hinv);
-        f[7] = fmad(k5, c7.x - c7.y, ld_h(s + 7 * pl + i7) * hinv);
-    } else {
-        (void)theta;
-        f[0] = T(ldg(s + 0 * pl + i0));
-        f[1] = T(ldg(s + 1 * pl + i1));
-        f[2] = T(ldg(s + 2 * pl + i2));
-        f[3] = T(ldg(s + 3 * pl + i3));
-        f[4] = T(ldg(s + 4 * pl + i4));
-        f[5] = T(ldg(s + 5 * pl + i5));
-        f[6] = T(ldg(s + 6 * pl + i6));
-        f[7] = T(ldg(s + 7 * pl + i7));
+        q.c[0] = ldg(c + i0);
+        q.c[1] = ldg(c + i1);
+        q.c[2] = ldg(c + i2);
+        q.c[3] = ldg(c + i3);
+        q.c[4] = ldg(c + i4);
+        q.c[5] = ldg(c + i5);
+        q.c[6] = ldg(c + i6);
+        q.c[7] = ldg(c + i7);
     }
+    q.p[0] = ldg(s + 0 * pl + i0);
+    q.p[1] = ldg(s + 1 * pl + i1);
+    q.p[2] = ldg(s + 2 * pl + i2);
+    q.p[3] = ldg(s + 3 * pl + i3);
+    q.p[4] = ldg(s + 4 * pl + i4);
+    q.p[5] = ldg(s + 5 * pl + i5);
+    q.p[6] = ldg(s + 6 * pl + i6);
+    q.p[7] = ldg(s + 7 * pl + i7);
+}
+
+// The pre-collision populations f_p(x) from the pulled stored values
+// (FP16S: deviation / scale + the equilibrium part of the source carrier).
+template <int S>
+__device__ __forceinline__ void pull_decode(const StepParams& a, const Pulled<S>& q,
+                                            typename StoreT<S>::T f[8], typename StoreT<S>::T theta) {
+    using T = typename StoreT<S>::T;
+    if constexpr (S == S_F16S) {
+        const float hinv = a.hinv;
+        const float k1 = 0.5f * (1.0f - theta), k5 = 0.25f * theta;
+        // (the FP16 value times the power-of-two 1/scale is exact)
+        f[0] = fmad(k1, q.c[0].x, __half2float(q.p[0]) * hinv);
+        f[1] = fmad(k1, q.c[1].y, __half2float(q.p[1]) * hinv);
+        f[2] = fmad(-k1, q.c[2].x, __half2float(q.p[2]) * hinv);
+        f[3] = fmad(-k1, q.c[3].y, __half2float(q.p[3]) * hinv);
+        f[4] = fmad(k5, q.c[4].x + q.c[4].y, __half2float(q.p[4]) * hinv);
+        f[5] = fmad(k5, q.c[5].y - q.c[5].x, __half2float(q.p[5]) * hinv);
+        f[6] = fmad(-k5, q.c[6].x + q.c[6].y, __half2float(q.p[6]) * hinv);
+        f[7] = fmad(k5, q.c[7].x - q.c[7].y, __half2float(q.p[7]) * hinv);
+    } else {
+        (void)a;
+        (void)theta;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) f[p] = T(q.p[p]);
+    }
+}
+
+// Gather the pre-collision populations of node (x, y): f_p(x) = f*_p(x - c_p).
+template <int S>
+__device__ __forceinline__ void gather(const StepParams& a, int64_t r0, int64_t rm, int64_t rp,
+                                       int x, int xm, int xp, typename StoreT<S>::T f[8],
+                                       typename StoreT<S>::T theta) {
+    Pulled<S> q;
+    pull_load<S>(a, r0, rm, rp, x, xm, xp, q);
+    pull_decode<S>(a, q, f, theta);
 }
 
 // FP16-shifted store of one node: the deviations N (unscaled, FP32) are
@@ -729,6 +760,146 @@ k_step3(const StepParams a, const Coef<float> c) {
     if (CHECK) residual_reduce<float>(a, acc);
 }
 
+// ---------------------------------------------------------------------------
+// Wavefront schedule of T pseudo-time steps per launch (FP32 or FP16-shifted
+// storage; T = 3 or 4).
+//
+// A block of 32*NW threads owns a strip of W = 32*NW slot columns (thread t
+// = column t for the whole launch) and a segment of `seg` output rows, and
+// walks down the segment one row per iteration at every step level at once:
+// in iteration i, step tau (1..T) updates row ybeg + i - 2*(tau - 1), so step
+// tau trails step tau - 1 by two rows and only reads rows that step tau - 1
+// finished in earlier iterations.  Step 1 pulls f*(t) from global memory,
+// steps 2..T-1 pull from and write to rings of kWvD = 4 rows per level in
+// shared memory (row y in ring slot y mod 4), and step T stores f*(t+T) of
+// the strip's W - 2(T-1) inner columns to global memory.  One block barrier
+// per iteration separates a ring slot's last read from its next write.  The
+// halo costs 2(T-1) of W columns and 2(T - tau) extra rows of level tau per
+// segment, against 64 x 16 slots per 60 x 12 outputs of the three-step tile,
+// and a level's ring holds four rows instead of a whole tile, so four steps
+// per launch fit.  The per-node arithmetic is the single step's: FP32 results
+// equal T single-step launches bit for bit (FP16S keeps the intermediate
+// states in FP32).  Plain steps only; lattices from W x 8 nodes up.
+#ifndef LBM_WV_NW
+#define LBM_WV_NW 8
+#endif
+constexpr int kWvNW = LBM_WV_NW;                 // warps per block
+constexpr int kWvW = 32 * kWvNW;                 // strip width (slot columns)
+constexpr int kWvD = 4;                          // ring rows per level
+constexpr int kWvSegDefault = 128;               // output rows per block segment (default)
+#ifndef LBM_WV_PREF
+#define LBM_WV_PREF 1
+#endif
+constexpr bool kWvPref = LBM_WV_PREF != 0;       // level-1 loads one iteration ahead
+template <int T> __host__ __device__ constexpr int wv_ox() { return kWvW - 2 * (T - 1); }
+template <int T> __host__ __device__ constexpr int wv_smem() { return (T - 1) * 8 * kWvD * kWvW * (int)sizeof(float); }
+// resident blocks per SM the kernel is compiled for: 228 KB of shared memory
+// per SM, 1 KB reserved per block
+template <int T> constexpr int wv_minb() {
+    return (233472 / (wv_smem<T>() + 1024)) < (2048 / kWvW) ? (233472 / (wv_smem<T>() + 1024))
+                                                             : (2048 / kWvW);
+}
+
+template <int S, bool GEN, int T>
+__global__ void __launch_bounds__(kWvW, wv_minb<T>())
+k_wave(const StepParams a, const Coef<float> c, int seg) {
+    static_assert(T >= 2 && T <= 4, "two to four steps per launch");
+    constexpr int W = kWvW, OX = wv_ox<T>(), PL = kWvD * kWvW;
+    extern __shared__ float wv_ring[];            // (T-1) rings of 8 planes x kWvD rows x W
+    const int nx = a.nx, ny = a.ny;
+    const int t = threadIdx.x;
+    const int nstrips = (nx + OX - 1) / OX;
+    const int strip = (int)(blockIdx.x % (unsigned)nstrips);
+    const int y0 = (int)(blockIdx.x / (unsigned)nstrips) * seg;
+    const int rows = min(seg, ny - y0);           // output rows of this segment
+    const int xs = strip * OX - (T - 1) + t;      // lattice column of slot t (unwrapped)
+    const int x = wrap_slot<false>(xs, nx);
+    const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
+    const bool store_ok = t >= T - 1 && t <= W - T && xs < nx;
+    const float* __restrict__ gxp = static_cast<const float*>(a.gx);
+    const float* __restrict__ gyp = static_cast<const float*>(a.gy);
+    const int ybeg = y0 - (T - 1);                // first row of level 1
+    const int iters = rows + 3 * (T - 1);
+    const int n1 = rows + 2 * (T - 1);            // rows of level 1
+    // Force of the thread's column in rows y1, y1 - 1, ..., y1 - 2(T - 1) (y1 the
+    // row of level 1 in this iteration): level tau uses entry 2(tau - 1), so no
+    // level waits on a force load.
+    constexpr int NH = 2 * (T - 1) + 1;
+    float hx[NH], hy[NH];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) hx[k] = hy[k] = 0.0f;
+    // Level 1 reads global memory LBM_WV_PREF rows ahead (0 or 1): the loads of
+    // row ybeg + i + 1 are then in flight while iteration i works from shared memory.
+    Pulled<S> q;
+    float qg[2] = {0.0f, 0.0f};
+    auto load1 = [&](int i) {
+        const int y = wrap_slot<false>(ybeg + i, ny);
+        const int64_t r0 = (int64_t)y * nx;
+        pull_load<S>(a, r0, (int64_t)wrap_dec(y, ny) * nx, (int64_t)wrap_inc(y, ny) * nx, x, xm, xp, q);
+        qg[0] = ldg(gxp + r0 + x);
+        qg[1] = ldg(gyp + r0 + x);
+    };
+    if (kWvPref) load1(0);
+    for (int i = 0; i < iters; ++i) {
+        // Level 1: rows ybeg .. y0 + rows - 1 + (T - 1), pulled from global memory.
+        const bool l1 = i < n1;
+        const int y1 = ybeg + i;
+        float f1[8];
+        if (!kWvPref && l1) load1(i);
+#pragma unroll
+        for (int k = NH - 1; k > 0; --k) {
+            hx[k] = hx[k - 1];
+            hy[k] = hy[k - 1];
+        }
+        hx[0] = qg[0];
+        hy[0] = qg[1];
+        if (l1) {
+            pull_decode<S>(a, q, f1, c.theta);
+            if (kWvPref && i + 1 < n1) load1(i + 1);
+        }
+        // Levels 2..T: row ybeg + i - 2(tau - 1), pulled from ring tau - 1.
+#pragma unroll
+        for (int tau = T; tau >= 2; --tau) {
+            // active rows y0 - (T - tau) .. y0 + rows - 1 + (T - tau)
+            if (i < 3 * (tau - 1) || i > rows + 2 * T + tau - 4) continue;
+            if (tau < T ? (t < tau - 1 || t > W - tau) : !store_ok) continue;
+            const int yl = ybeg + i - 2 * (tau - 1);
+            const float* s = wv_ring + (tau - 2) * 8 * PL + t;
+            const int rm = ((yl - 1) & (kWvD - 1)) * W, r0 = (yl & (kWvD - 1)) * W,
+                      rp = ((yl + 1) & (kWvD - 1)) * W;
+            float f[8];
+            f[0] = s[0 * PL + r0 - 1];          // f_p(x) = f*_p(x - c_p)
+            f[1] = s[1 * PL + rm];
+            f[2] = s[2 * PL + r0 + 1];
+            f[3] = s[3 * PL + rp];
+            f[4] = s[4 * PL + rm - 1];
+            f[5] = s[5 * PL + rm + 1];
+            f[6] = s[6 * PL + rp + 1];
+            f[7] = s[7 * PL + rp - 1];
+            float u, v;
+            const Mom<float> m =
+                collide<float, GEN>(moments(f), hx[2 * (tau - 1)], hy[2 * (tau - 1)], c, u, v);
+            if (tau < T) {
+                float fs[8];
+                populations(m, fs);
+                float* d = wv_ring + (tau - 1) * 8 * PL + r0 + t;
+#pragma unroll
+                for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
+            } else {
+                scatter_local<S>(a, (int64_t)yl * nx + xs, m, c.qtheta);   // yl in [0, ny), xs < nx
+            }
+        }
+        if (l1) {
+            float u, v, fs[8];
+            populations(collide<float, GEN>(moments(f1), hx[0], hy[0], c, u, v), fs);
+            float* d = wv_ring + (y1 & (kWvD - 1)) * W + t;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
+        }
+        __syncthreads();
+    }
+}
+
 // Solution fields of the current state (Table 2, Eq. compute_bared), FP64:
 // out planes u_x, u_y, sigma_xx, sigma_yy, sigma_xy (stride nx*ny).
 template <int S>
@@ -905,6 +1076,20 @@ inline bool step3_fits(int nx, int ny) { return nx >= kT3W && ny >= kT3H; }
 inline int64_t step3_tiles(int nx, int ny) {
     return (int64_t)((nx + kT3OX - 1) / kT3OX) * ((ny + kT3OY - 1) / kT3OY);
 }
+
+// Wavefront launches (k_wave) of a single lattice: from one strip width by 8
+// rows up (the slot wrap is a single conditional subtraction there).
+inline bool wave_fits(int nx, int ny) { return nx >= kWvW && ny >= 8; }
+
+template <int T>
+inline int64_t wave_blocks(int nx, int ny, int seg) {
+    return (int64_t)((nx + wv_ox<T>() - 1) / wv_ox<T>()) * ((ny + seg - 1) / seg);
+}
+
+// T fused plain steps on the wavefront schedule (T = 3 or 4); defined with
+// each storage type's kernels.
+cudaError_t wave_f32(const StepParams& a, const Coef<float>& c, bool gen, int T, int seg, cudaStream_t st);
+cudaError_t wave_f16s(const StepParams& a, const Coef<float>& c, bool gen, int T, int seg, cudaStream_t st);
 
 // Three fused steps (k_step3); defined with each storage type's kernels.
 cudaError_t step3_f32(const StepParams& a, const Coef<float>& c, bool gen, bool check,

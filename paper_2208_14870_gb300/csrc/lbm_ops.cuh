@@ -75,6 +75,47 @@ static cudaError_t launch_step3(const StepParams& a, const Coef<float>& c, bool 
     return cudaGetLastError();
 }
 
+template <int S>
+static cudaError_t wv_allow_smem() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    e = cudaFuncSetAttribute(k_wave<S, false, 3>, at, wv_smem<3>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wave<S, true, 3>, at, wv_smem<3>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wave<S, false, 4>, at, wv_smem<4>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wave<S, true, 4>, at, wv_smem<4>());
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+// T = 3 or 4 fused plain steps on the wavefront schedule: one block per strip
+// and segment of seg output rows (the caller checks wave_fits).
+template <int S>
+static cudaError_t launch_wave(const StepParams& a, const Coef<float>& c, bool gen, int T, int seg,
+                               cudaStream_t st) {
+    if ((T != 3 && T != 4) || seg < 1 || !wave_fits(a.nx, a.ny)) return cudaErrorInvalidValue;
+    cudaError_t e = wv_allow_smem<S>();
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = T == 3 ? wave_blocks<3>(a.nx, a.ny, seg) : wave_blocks<4>(a.nx, a.ny, seg);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned int grid = (unsigned int)blocks;
+    const dim3 block(kWvW);
+    if (T == 3) {
+        if (gen) k_wave<S, true, 3><<<grid, block, wv_smem<3>(), st>>>(a, c, seg);
+        else k_wave<S, false, 3><<<grid, block, wv_smem<3>(), st>>>(a, c, seg);
+    } else {
+        if (gen) k_wave<S, true, 4><<<grid, block, wv_smem<4>(), st>>>(a, c, seg);
+        else k_wave<S, false, 4><<<grid, block, wv_smem<4>(), st>>>(a, c, seg);
+    }
+    return cudaGetLastError();
+}
+
 // Two fused steps: one block per tile (check: up to check_blocks blocks).
 template <int S>
 static cudaError_t launch_step2(const StepParams& a, const Coef<float>& c, bool gen, bool check,

@@ -59,6 +59,8 @@ _SIGS = {
     "lbm_set_stream": (_c.c_int, [_vp, _vp]),
     "lbm_set_steps_per_launch": (_c.c_int, [_vp, _c.c_int]),
     "lbm_get_steps_per_launch": (_c.c_int, [_vp, _c.POINTER(_c.c_int)]),
+    "lbm_set_wavefront": (_c.c_int, [_vp, _c.c_int]),
+    "lbm_get_wavefront": (_c.c_int, [_vp, _c.POINTER(_c.c_int)]),
     "lbm_set_force": (_c.c_int, [_vp, _vp, _vp]),
     "lbm_set_force_device": (_c.c_int, [_vp, _vp, _vp]),
     "lbm_set_force_corrected": (_c.c_int, [_vp, _vp, _vp, _vp]),
@@ -154,6 +156,16 @@ def lbm_get_steps_per_launch(ctx: int) -> int:
     k = _c.c_int()
     _check(_lib.lbm_get_steps_per_launch(ctx, _c.byref(k)), "lbm_get_steps_per_launch")
     return k.value
+
+
+def lbm_set_wavefront(ctx: int, rows: int) -> None:
+    _check(_lib.lbm_set_wavefront(ctx, rows), "lbm_set_wavefront")
+
+
+def lbm_get_wavefront(ctx: int) -> int:
+    r = _c.c_int()
+    _check(_lib.lbm_get_wavefront(ctx, _c.byref(r)), "lbm_get_wavefront")
+    return r.value
 
 
 def lbm_set_force(ctx: int, gx_ptr: int, gy_ptr: int) -> None:
@@ -392,6 +404,16 @@ class Lattice:
     @steps_per_launch.setter
     def steps_per_launch(self, k: int):
         lbm_set_steps_per_launch(self.ctx, k)
+
+    @property
+    def wavefront(self) -> int:
+        """Rows per block segment of the wavefront schedule (-1: chosen per
+        launch, 0: tile schedule)."""
+        return lbm_get_wavefront(self.ctx)
+
+    @wavefront.setter
+    def wavefront(self, rows: int):
+        lbm_set_wavefront(self.ctx, rows)
 
     @property
     def rates(self) -> dict:

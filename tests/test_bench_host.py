@@ -18,18 +18,22 @@ def bench():
     return mod
 
 
-def simulate_launches(iters, check_every, spl):
+def simulate_launches(iters, check_every, spl, wave=False):
     """Launch sequence of lbm_iterate_checked from step 0, written out launch
     by launch as the library plans it: plain steps grouped into launches of spl
-    steps, leftovers in launches of 2 or 1, and a check step (index + 1 a
-    multiple of check_every) as the last step of a launch of at most two
-    steps."""
+    steps (four only on the wavefront schedule, else three), leftovers in
+    shorter launches, and a check step (index + 1 a multiple of check_every)
+    as the last step of a launch of at most two steps."""
+    big = 4 if spl >= 4 and wave else min(spl, 3)
+
     def plain(m):
         count = 0
         while m > 0:
-            k = min(spl, m)
-            if spl == 3 and m == 4:
+            k = min(big, m)
+            if big == 3 and m == 4:
                 k = 2          # 4 = 2 + 2 instead of 3 + 1
+            if big == 4 and m == 5:
+                k = 3          # 5 = 3 + 2 instead of 4 + 1
             m -= k
             count += 1
         return count
@@ -46,14 +50,34 @@ def simulate_launches(iters, check_every, spl):
     return launches
 
 
-@pytest.mark.parametrize("spl", [1, 2, 3])
-def test_launch_count_matches_the_schedule(bench, spl):
-    for iters in (0, 1, 2, 7, 99, 100, 101, 1000, 1234):
-        for ce in (1, 2, 3, 7, 10, 100):
-            assert bench.launches_per_iterate(iters, ce, spl) == simulate_launches(iters, ce, spl), (iters, ce)
+@pytest.mark.parametrize("spl,wave", [(1, False), (2, False), (3, False), (3, True), (4, False), (4, True)])
+def test_launch_count_matches_the_schedule(bench, spl, wave):
+    for iters in (0, 1, 2, 5, 7, 9, 99, 100, 101, 1000, 1234):
+        for ce in (1, 2, 3, 6, 7, 10, 11, 100):
+            assert (bench.launches_per_iterate(iters, ce, spl, wave)
+                    == simulate_launches(iters, ce, spl, wave)), (iters, ce)
     assert bench.launches_per_iterate(1000, 100, 2) == 500
     assert bench.launches_per_iterate(1000, 100, 1) == 1000
     assert bench.launches_per_iterate(1000, 100, 3) == 10 * (33 + 1)   # 98 = 32 x 3 + 2, then the check pair
+    assert bench.launches_per_iterate(1000, 100, 4, True) == 10 * (25 + 1)   # 98 = 24 x 4 + 2
+
+
+def test_dominant_block(bench):
+    # the first steps of a window that run as whole launches of the longest kind
+    assert bench.dominant_block(100, 1) == (99, 1)
+    assert bench.dominant_block(100, 2) == (98, 2)
+    assert bench.dominant_block(100, 3) == (96, 3)
+    assert bench.dominant_block(100, 4) == (96, 3)          # four steps need the wavefront schedule
+    assert bench.dominant_block(100, 4, True) == (96, 4)
+    assert bench.dominant_block(21, 3) == (15, 3)          # 19 = 5 x 3 + 2 + 2
+    assert bench.dominant_block(11, 4, True) == (4, 4)      # 9 = 4 + 3 + 2
+    for ce in range(1, 40):
+        for spl, wave in ((1, False), (2, False), (3, False), (4, True)):
+            block, big = bench.dominant_block(ce, spl, wave)
+            rest = bench.plan_plain(ce - min(spl, 2, ce) - block, spl, wave)
+            assert bench.plan_plain(block, spl, wave) == [big] * (block // big)
+            assert sorted(bench.plan_plain(block, spl, wave) + rest, reverse=True) == \
+                sorted(bench.plan_plain(ce - min(spl, 2, ce), spl, wave), reverse=True)
 
 
 def test_kernel_hash_ignores_comments_but_not_code(bench, tmp_path):

@@ -96,23 +96,25 @@ def test_two_step_matches_oracle():
 
 
 def test_steps_per_launch_availability():
-    """Default: three steps from 64 x 16 on for FP32 and FP16S; any FP32/FP16S
-    lattice may choose one to three; FP64 always one."""
+    """Default for FP32 and FP16S: four steps from 256 x 8 on (wavefront
+    schedule), else three from 64 x 16; any FP32/FP16S lattice may
+    choose one to four; FP64 always one."""
     lam, mu = W.lame_2d(1.0, 0.3)
-    for nx, ny, dt, want in ((64, 16, "f32", 3), (63, 32, "f32", 1), (64, 15, "f32", 1),
-                             (256, 256, "f64", 1), (256, 256, "f16s", 3), (63, 64, "f16s", 1)):
+    for nx, ny, dt, want in ((64, 16, "f32", 3), (63, 32, "f32", 1), (64, 15, "f32", 1), (255, 64, "f32", 3),
+                             (256, 8, "f32", 4), (256, 7, "f16s", 1), (300, 20, "f16s", 4),
+                             (256, 256, "f64", 1), (256, 256, "f16s", 4), (63, 64, "f16s", 1)):
         with Lattice(nx, ny, lam, mu, dt) as lat:
             assert lat.steps_per_launch == want, (nx, ny, dt)
             lat.steps_per_launch = 1
             if dt == "f64":
-                for k in (2, 3):
+                for k in (2, 3, 4):
                     with pytest.raises(P.LBMError):
                         lat.steps_per_launch = k
             else:
-                for k in (2, 3):
+                for k in (2, 3, 4):
                     lat.steps_per_launch = k
                     assert lat.steps_per_launch == k
-            for k in (0, 4):
+            for k in (0, 5):
                 with pytest.raises(P.LBMError):
                     lat.steps_per_launch = k
 
@@ -175,7 +177,9 @@ def test_two_step_f16s_conserves_mean_displacement():
         assert abs(float(np.mean(u[0]))) < 1e-4 * scale and abs(float(np.mean(u[1]))) < 1e-4 * scale
 
 
-# Three steps per launch: tile 60 x 12 nodes, slot arrays 64 x 16.
+# Three steps per launch on the tile schedule (the wavefront schedule is
+# switched off; its tests are in test_gpu_wavefront.py): tile 60 x 12 nodes,
+# slot arrays 64 x 16.
 @pytest.mark.parametrize("nx,ny", [(64, 16), (130, 70), (517, 33), (64, 300), (1, 1), (5, 5), (63, 15), (7, 130)])
 @pytest.mark.parametrize("steps", [1, 2, 3, 7, 11])
 def test_three_step_launch_is_bit_identical(nx, ny, steps):
@@ -186,6 +190,7 @@ def test_three_step_launch_is_bit_identical(nx, ny, steps):
     for spl in (1, 3):
         with Lattice(nx, ny, lam, mu, "f32") as lat:
             lat.steps_per_launch = spl
+            lat.wavefront = 0
             lat.set_force(gx, gy)
             lat.iterate(steps)
             assert lat.step == steps
@@ -203,6 +208,7 @@ def test_three_step_checked_windows_and_solve(check_every):
     for spl in (1, 3):
         with Lattice(nx, ny, lam, mu, "f32", tau12=0.9, tau22=0.3) as lat:
             lat.steps_per_launch = spl
+            lat.wavefront = 0
             lat.set_force(gx, gy)
             r = lat.iterate_checked(41, check_every)
             s = lat.solve(1e-6, 200000, 100)
@@ -224,6 +230,7 @@ def test_three_step_f16s_matches_single_step_and_oracle(nx, ny):
     for spl in (1, 3):
         with Lattice(nx, ny, lam, mu, "f16s") as lat:
             lat.steps_per_launch = spl
+            lat.wavefront = 0
             lat.set_force(gx, gy)
             lat.iterate_checked(steps, 7)
             out[spl] = lat.fields()
