@@ -61,6 +61,13 @@ FP64_PEAK_GINST = 625.0
 # count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
 # small launch are not counted, so these slightly undercount.
 NCU_TRAFFIC = {
+    # four-step wavefront kernel: captured at 4096^2, where the segments are 32 rows long and
+    # neighbouring segments both read 6 of every 38 level-1 rows; at 16384^2 (128-row segments)
+    # that share is smaller, so the capture does not scale to the full launch: traffic stays null
+    # and the capture's figures are kept beside it
+    "f32_x4w": {"bytes_per_launch": None, "kernel_hash": "1a1de473db230565",
+                "ncu": {"case": "4096^2, 32-row segments", "dram_bytes_per_launch": 776.318976e6 + 491.771392e6,
+                        "dram_throughput_pct": 51.3, "issue_active_pct": 63.7, "top_stall": "long_scoreboard"}},
     "f32_x3": {"bytes_per_launch": (673.150976e6 + 498.287616e6) * 16, "kernel_hash": "72ac5d7b008eb4b5",
                "ncu": {"dram_throughput_pct": 58.9, "issue_active_pct": 62.9, "top_stall": "not_selected"}},
     "f16s_x3": {"bytes_per_launch": (538.608128e6 + 366.969344e6) * 16, "kernel_hash": "72ac5d7b008eb4b5",
