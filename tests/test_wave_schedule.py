@@ -65,6 +65,7 @@ def _wave(state, gx, gy, T, seg, W, D):
         ybeg = y0 - (T - 1)
         for i in range(rows + 3 * (T - 1)):
             writes = []                                # applied after the block barrier
+            reads = set()                              # ring slots read in this iteration
             for tau in range(T, 1, -1):
                 if i < 3 * (tau - 1) or i > rows + 2 * T + tau - 4:
                     continue
@@ -72,6 +73,7 @@ def _wave(state, gx, gy, T, seg, W, D):
                 act = store_ok if tau == T else (t >= tau - 1) & (t <= W - tau)
                 for dy in (-1, 0, 1):
                     assert held[tau - 2][(yl + dy) % D] == yl + dy
+                    reads.add((tau - 2, (yl + dy) % D))
                 f = np.empty((8, int(act.sum())))
                 for p, (cx, cy) in enumerate(C):
                     cols = t[act] - cx
@@ -93,6 +95,9 @@ def _wave(state, gx, gy, T, seg, W, D):
                 for p, (cx, cy) in enumerate(C):
                     f[p] = state[p][(y - cy) % ny][(x - cx) % nx]
                 writes.append((0, y1, np.ones(W, bool), _toy(f, gx[y, x], gy[y, x])))
+            # threads of one iteration are not ordered: no slot may be both
+            # read and written between two barriers
+            assert not reads & {(lv, yl % D) for lv, yl, _, _ in writes}
             for lv, yl, act, g in writes:
                 ring[lv][:, yl % D, :] = np.nan
                 ring[lv][:, yl % D, act] = g
@@ -125,8 +130,8 @@ def test_wavefront_schedule_equals_single_steps(W, T, dnx, ny, seg):
 
 def test_ring_depth_is_the_minimum():
     """Level j + 1 reads rows r - 3 .. r - 1 of level j while level j writes
-    row r in the same iteration: with three ring rows the replay must find a
-    ring slot that no longer holds the row it needs."""
+    row r in the same iteration: with three ring rows the slot of row r - 3
+    is read and written between the same two barriers."""
     assert D == 4
     rng = np.random.default_rng(5)
     nx, ny = 40, 12
