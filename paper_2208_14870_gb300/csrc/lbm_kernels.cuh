@@ -777,9 +777,14 @@ k_step3(const StepParams a, const Coef<float> c) {
 // halo costs 2(T-1) of W columns and 2(T - tau) extra rows of level tau per
 // segment, against 64 x 16 slots per 60 x 12 outputs of the three-step tile,
 // and a level's ring holds four rows instead of a whole tile, so four steps
-// per launch fit.  The per-node arithmetic is the single step's: FP32 results
-// equal T single-step launches bit for bit (FP16S keeps the intermediate
-// states in FP32).  Plain steps only; lattices from W x 8 nodes up.
+// per launch fit.  Latency: the force of a thread's column for the last
+// 2(T-1)+1 rows stays in registers (step tau uses the row step 1 loaded
+// 2(tau-1) iterations earlier), and step 1 issues the loads of its next row
+// before the shared-memory work of the current iteration (LBM_WV_PREF), so
+// no level waits on a global load it has just issued.  The per-node
+// arithmetic is the single step's: FP32 results equal T single-step launches
+// bit for bit (FP16S keeps the intermediate states in FP32).  Plain steps
+// only; lattices from W x 8 nodes up.
 #ifndef LBM_WV_NW
 #define LBM_WV_NW 8
 #endif
