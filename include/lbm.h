@@ -179,8 +179,10 @@ int lbm_set_force_device(lbm_ctx *ctx, const double *gx, const double *gy);
  * + g(x-1,y-1))/4.  d = {D1, D2, D3} (host, finite).  gx, gy as in
  * lbm_set_force.  Synchronous.  The caller chooses D: the constants printed in
  * Appendix B (lbm_error_constants) do not cancel the force-driven leading
- * error of this scheme as printed (see the design notes), so they are an
- * input here rather than computed. */
+ * error of this scheme as printed (D1 and D2 carry misprints, and the printed
+ * constants have the opposite sign of the error equation as written), so they
+ * are an input here rather than computed; d = -(D1, D2, D3) of lbm_error_constants_scheme
+ * cancels it (about ten times smaller errors at nu = 0.8, E = 0.085, Sec. 6.3.2). */
 int lbm_set_force_corrected(lbm_ctx *ctx, const double *gx, const double *gy, const double *d);
 
 /* The leading-order error constants as printed in Appendix B:
@@ -189,6 +191,32 @@ int lbm_set_force_corrected(lbm_ctx *ctx, const double *gx, const double *gy, co
  * times tau12 = tau21 (0 = 1/2) and tau22 (0 = 1/2).  Host-only arithmetic. */
 int lbm_error_constants(double E, double nu, double theta, double tau12, double tau22,
                         double *out);
+
+/* The same constants of the scheme itself: Appendix B with three misprints
+ * read, so that they equal the exact discrete leading error of this scheme
+ * (extracted from its one-step operator: decay rates and eigenvectors of
+ * free plane waves for C1..C5, steady states for D1..D3).  C2's E^3 term is
+ * divided by 8 theta (1 - theta^2)(1 - nu^2)^3 as are those of C3 and C4
+ * (printed: 8 (1 - theta^2)(1 - nu^2)^3); the E terms of D1 and D2 are divided
+ * by (1 - theta^2)(1 - nu^2) and 2 (1 - theta^2)(1 - nu^2) (printed:
+ * (1 - nu^2)^2).  The other five are the printed ones.  As printed, the
+ * constants carry the opposite sign of the error source of Eq. ux_order2, so
+ * the correction that cancels the force-driven leading error (the improved
+ * scheme of Sec. 6.3.2) is lbm_set_force_corrected with d = -(D1, D2, D3).
+ * Arguments and errors as lbm_error_constants.  Host-only arithmetic. */
+int lbm_error_constants_scheme(double E, double nu, double theta, double tau12, double tau22,
+                               double *out);
+
+/* Relaxation times of the fourth-order special case (Sec. 6.3.3): tau12 =
+ * tau21 as in Appendix C, which zeroes C5, and tau22 such that C1 of Appendix
+ * B vanishes too (C1 is linear in tau22; the tau22 printed in Appendix C does
+ * not zero it).  With both zero and the force correction d = -(D1, D2, D3) of
+ * lbm_error_constants_scheme, a displacement field without mixed fourth
+ * derivatives converges at fourth order.  Pass them in lbm_options; check
+ * stability with lbm_spectral_radius (large regions of (E, nu) are unstable,
+ * Sec. 6.3.3).  theta 0 = 1/3.  Host-only; LBM_ERR_ARG for E <= 0, nu outside
+ * (-1, 1), theta outside (0, 1) or nu = theta. */
+int lbm_fourth_order_taus(double E, double nu, double theta, double *tau12, double *tau22);
 
 /* Von Neumann stability (Sec. 4): sup over sampled wave vectors
  * k = khat (cos phi, sin phi), khat in [0, pi] (nk >= 2 points), phi in

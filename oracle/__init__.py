@@ -22,18 +22,19 @@ Parts:
     spectral radius (Sec. 4), and the exact discrete steady state mode by
     mode.
 
-  * Sec. 4 / Appendices B and C helpers: the printed error constants, the
-    finite-difference force correction, and the exact-discrete leading error
-    of axis-aligned modes.
+  * Sec. 4 / Appendices B and C helpers: the printed error constants and
+    their read form, the finite-difference force correction, the exact
+    discrete leading error (axis-aligned modes, and every constant of
+    Appendix B from the one-step operator), and the relaxation times of the
+    fourth-order case.
 
 Every function here is pinned by ``tests/test_oracle_*.py`` against the
 paper's printed values, closed forms, brute force on small lattices and exact
-invariants, with one exception: in ``error_constants_printed`` only the
-combinations C5 - mu D3 (all parameters) and C1 - (mu + K) D1 (at nu = 0) are
-pinned against the scheme's exact discrete leading error; C2, C3, C4 and D2
-enter only combinations that steady states cannot separate and are "parity
-unpinned" (transcribed as printed, cross-checked against an independent C
-transcription only).
+invariants.  The constants of Appendix B are pinned one by one against the
+scheme's exact discrete leading error (``leading_error_exact``, extracted
+from the one-step operator), which shows three misprints (C2, D1, D2, applied
+in ``error_constants_read``) and a fourth one in Appendix C's tau_22
+(``fourth_order_taus_scheme``).
 """
 from __future__ import annotations
 
@@ -133,6 +134,29 @@ def fourth_order_taus(lam: float, mu: float, theta: float = THETA_STANDARD) -> t
                        - 6.0 * (1.0 - theta ** 2) * ts ** 2))
     den = 2.0 * theta * (2.0 - 3.0 * theta + 12.0 * theta * t11 ** 2) * (ts - td)
     return tau12, num / den
+
+
+def fourth_order_taus_scheme(lam: float, mu: float, theta: float = THETA_STANDARD) -> tuple[float, float]:
+    """tau_12 = tau_21 and tau_22 that zero both C5 and C1 of this scheme
+    (Sec. 6.3.3: with the force correction, a field without mixed fourth
+    derivatives then converges at fourth order).  tau_12 is Appendix C's (it
+    zeroes C5, whose printed form is the scheme's); tau_22 solves C1 = 0 with
+    the C1 of Appendix B (also the scheme's), which is linear in tau_22:
+    12 theta (theta - nu) tau12 tau22 = 1 - theta^2
+        - 12 (1 - theta^2)(1 - nu^2) (a3 E^2 + a2 tau12 E),
+    a3 = (nu^2 - 2 theta nu + 1) / ((1 - theta^2)(1 - nu^2)^3),
+    a2 = theta (nu - theta) / ((1 - theta^2)(1 - nu^2)^2), with E~ and nu from
+    (lam, mu) by the 2D relations.  (Appendix C's printed tau_22 does not zero
+    C1.)"""
+    tau12, _ = fourth_order_taus(lam, mu, theta)
+    nu = lam / (lam + 2.0 * mu)
+    E = (lam + 2.0 * mu) * (1.0 - nu * nu)
+    th = theta
+    c, d = 1.0 - th * th, 1.0 - nu * nu
+    a3 = (nu * nu - 2.0 * th * nu + 1.0) / (c * d ** 3)
+    a2 = th * (nu - th) / (c * d ** 2)
+    tau22 = (1.0 - th * th - 12.0 * c * d * (a3 * E * E + a2 * tau12 * E)) / (12.0 * th * (th - nu) * tau12)
+    return tau12, tau22
 
 
 # ----------------------------------------------------------------------------
@@ -309,6 +333,140 @@ def error_constants_printed(E: float, nu: float, theta: float = THETA_STANDARD,
           - q * t21 / (2 * c * d ** 2) * E - th / 2)
     D3 = E ** 2 / (4 * th * (1 + nu) ** 2) + t12 / (2 * (1 + nu)) * E - th / 4
     return np.array([C1, C2, C3, C4, C5, D1, D2, D3])
+
+
+def error_constants_read(E: float, nu: float, theta: float = THETA_STANDARD,
+                         tau12: float = 0.5, tau21: float | None = None,
+                         tau22: float = 0.5) -> np.ndarray:
+    """[C1..C5, D1..D3] of Appendix B with the readings of three misprints
+    applied (the scheme's exact discrete leading error, ``leading_error_exact``,
+    decides them):
+
+    * C2: the E^3 term is divided by 8 theta (1 - theta^2)(1 - nu^2)^3, like the
+      E^3 terms of C3 and C4 (printed: 8 (1 - theta^2)(1 - nu^2)^3);
+    * D1: the E term is theta (nu - theta) tau12 E / ((1 - theta^2)(1 - nu^2))
+      (printed: (1 - nu^2)^2 in the denominator);
+    * D2: the E term is -q tau21 E / (2 (1 - theta^2)(1 - nu^2)) with
+      q = theta^2 (1 + nu) + nu - 2 theta - 1 (printed: (1 - nu^2)^2).
+
+    The other five constants are the printed ones."""
+    th = theta
+    t21 = tau12 if tau21 is None else tau21
+    c, d = 1.0 - th * th, 1.0 - nu * nu
+    q = th * th * (1.0 + nu) + nu - 2.0 * th - 1.0
+    out = error_constants_printed(E, nu, theta=theta, tau12=tau12, tau21=tau21, tau22=tau22).copy()
+    p2 = ((1 - nu) ** 3 + 4 * th * (nu ** 3 - nu ** 2 + 3 * nu + 1)
+          + th ** 2 * (5 * nu ** 3 - 15 * nu ** 2 - nu - 5))
+    out[1] += p2 * E ** 3 * (1.0 / (8 * th * c * d ** 3) - 1.0 / (8 * c * d ** 3))
+    out[5] += th * (nu - th) * tau12 * E * (1.0 / (c * d) - 1.0 / (c * d ** 2))
+    out[6] += -q * t21 * E * (1.0 / (2 * c * d) - 1.0 / (2 * c * d ** 2))
+    return out
+
+
+def leading_error_exact(E: float, nu: float, theta: float = THETA_STANDARD,
+                        tau12: float = 0.5, tau22: float = 0.5,
+                        ks: tuple[float, float] = (0.01, 0.02)) -> tuple[np.ndarray, dict]:
+    """[C1..C5, D1..D3] of the scheme itself, from its exact one-step operator
+    (``fourier.amplification_matrix``), in the sign convention of Appendix B.
+
+    Eq. ux_order2 (and its y twin) says that the displacement of a plane wave
+    u = U exp(i k.x), k = kappa (c, s), obeys to O(kappa^4)
+        d/dt U = (-M(k) + sigma A(k)) U + (1 - sigma Dm(k)) g_hat,
+    with M the Navier-Cauchy symbol (mu kappa^2 + K k k^T), A the symbol of the
+    C-terms (A_xx = C1 c^4 + C3 c^2 s^2 + C5 s^4, A_xy = C2 c^3 s + C4 c s^3,
+    A_yx = C2 c s^3 + C4 c^3 s, A_yy = C1 s^4 + C3 c^2 s^2 + C5 c^4, times
+    kappa^4), Dm that of the D-terms, and sigma = -1 (the sign reading of the
+    printed constants).  Per time step (lattice units):
+
+    * free decay (g = 0): the two slow eigenvalues of the one-step operator
+      have log lambda = -s_j kappa^2 + sigma l_j kappa^4 with
+      l_L = C1 (c^6 + s^6) + (C2 + C3 + C4 + C5) c^2 s^2 and
+      l_T = C5 (c^6 + s^6) + (C1 + C3 - C2 - C4) c^2 s^2 (first-order
+      perturbation of the symmetric M): c = 1 gives C1 and C5, c = s gives C3
+      and C2 + C4;
+    * the displacement of the slow eigenvectors tilts from k (resp. k-perp)
+      by sigma kappa^2 cs (c^2 - s^2)(C5 - C1 + C4) / (-K) (longitudinal) and
+      sigma kappa^2 cs (c^2 - s^2)(C5 - C1 + C2) / K (transverse): at
+      tan(phi) = 1/2 these give C4 and C2 separately;
+    * steady state for g = M U0: U - U0 = sigma M^-1 (A - Dm M) U0, whose
+      entries give E1 = C1 - (mu + K) D1, E5 = C5 - mu D3,
+      E2 = C2 - K D1 - mu D2 and, as checks, E3 = C3 - mu D1 - (mu + K) D3 - K D2
+      and E4 = C4 - K D3 - (mu + K) D2.
+
+    Each coefficient is extrapolated to kappa -> 0 from kappa = ks (Richardson
+    in kappa^2).  The dict holds the three over-determined checks (C2 + C4
+    from the eigenvalues minus the sum from the tilts, and the residuals of
+    the E3 and E4 relations), which vanish when the structure of Eq. ux_order2
+    holds."""
+    from . import fourier as F
+    lam, mu = lame_2d(E, nu)
+    K = lam + mu
+    rates = relaxation_rates(lam, mu, theta=theta, tau12=tau12, tau22=tau22)
+    Mm = F.moment_matrix()
+
+    def extrapolate(f):
+        a, b = f(ks[0]), f(ks[1])
+        return (4.0 * a - b) / 3.0
+
+    def slow_modes(phi, kappa):
+        cph, sph = np.cos(phi), np.sin(phi)
+        vL, vT = np.array([cph, sph]), np.array([-sph, cph])
+        w, V = np.linalg.eig(F.amplification_matrix(rates, kappa * cph, kappa * sph))
+        out = {}
+        for j in np.argsort(-np.abs(w))[:2]:
+            U = Mm[:2] @ V[:, j]
+            kind = "L" if abs(np.vdot(vL, U)) > abs(np.vdot(vT, U)) else "T"
+            own, other = (vL, vT) if kind == "L" else (vT, vL)
+            out[kind] = (float(np.log(w[j]).real), float((np.vdot(other, U) / np.vdot(own, U)).real))
+        return out
+
+    def rate(phi, kind):
+        s2 = (mu + K) if kind == "L" else mu
+        return extrapolate(lambda kap: (slow_modes(phi, kap)[kind][0] + s2 * kap * kap) / kap ** 4)
+
+    def tilt(phi, kind):
+        return extrapolate(lambda kap: slow_modes(phi, kap)[kind][1] / kap ** 2)
+
+    sigma = -1.0
+    C1, C5 = sigma * rate(0.0, "L"), sigma * rate(0.0, "T")
+    SL, ST = 4.0 * sigma * rate(np.pi / 4, "L"), 4.0 * sigma * rate(np.pi / 4, "T")
+    C3 = (SL + ST) / 2.0 - C1 - C5
+    phi = np.arctan(0.5)
+    g = np.cos(phi) * np.sin(phi) * (np.cos(phi) ** 2 - np.sin(phi) ** 2)    # = 0.24
+    C4 = sigma * tilt(phi, "L") * (-K) / g - C5 + C1
+    C2 = sigma * tilt(phi, "T") * K / g - C5 + C1
+
+    A = F.operator(rates)
+    Bx, By = F.force_vectors(rates)
+
+    def steady_Q(ph, kappa):
+        cph, sph = np.cos(ph), np.sin(ph)
+        kx, ky = kappa * cph, kappa * sph
+        Mk = np.array([[mu * kappa ** 2 + K * kx * kx, K * kx * ky],
+                       [K * kx * ky, mu * kappa ** 2 + K * ky * ky]])
+        S = F.shift_diag(kx, ky)
+        cols = []
+        for U0 in (np.array([1.0, 0.0]), np.array([0.0, 1.0])):
+            gh = Mk @ U0
+            fh = np.linalg.solve(np.eye(8) - S[:, None] * A, S * (Bx * gh[0] + By * gh[1]))
+            U = Mm[:2] @ fh + 0.5 * gh              # u = m_10 + g/2 (Table 2)
+            cols.append(sigma * (Mk @ (U - U0)).real / kappa ** 4)
+        return np.stack(cols, axis=1)
+
+    Q0 = extrapolate(lambda kap: steady_Q(0.0, kap))
+    Qp = extrapolate(lambda kap: steady_Q(phi, kap))
+    E1, E5 = Q0[0, 0], Q0[1, 1]
+    cph, sph = np.cos(phi), np.sin(phi)
+    E3 = (Qp[0, 0] - E1 * cph ** 4 - E5 * sph ** 4) / (cph * cph * sph * sph)
+    E2, E4 = np.linalg.solve(np.array([[cph ** 3 * sph, cph * sph ** 3], [cph * sph ** 3, cph ** 3 * sph]]),
+                             np.array([Qp[0, 1], Qp[1, 0]]))
+    D1 = (C1 - E1) / (mu + K)
+    D3 = (C5 - E5) / mu
+    D2 = (C2 - K * D1 - E2) / mu
+    checks = {"C2+C4": (SL - ST) / 2.0 - (C2 + C4),
+              "E3": C3 - mu * D1 - (mu + K) * D3 - K * D2 - E3,
+              "E4": C4 - K * D3 - (mu + K) * D2 - E4}
+    return np.array([C1, C2, C3, C4, C5, D1, D2, D3]), checks
 
 
 def corrected_force_fd(gx: np.ndarray, gy: np.ndarray, D) -> tuple[np.ndarray, np.ndarray]:

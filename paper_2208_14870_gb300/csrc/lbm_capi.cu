@@ -604,14 +604,21 @@ int lbm_set_force_corrected(lbm_ctx* c, const double* gx, const double* gy, cons
     return LBM_OK;
 }
 
-int lbm_error_constants(double E, double nu, double theta, double tau12, double tau22, double* out) {
-    if (!out) return fail(LBM_ERR_ARG, "lbm_error_constants: null output");
+namespace {
+
+// Appendix B (tau_21 = tau_12): as printed, or (scheme) with the three
+// misprints read so that the constants are those of the scheme's exact
+// discrete leading error: C2's E^3 term over 8 theta (1 - theta^2)(1 - nu^2)^3
+// (printed without theta), and the E terms of D1 and D2 over (1 - theta^2)
+// (1 - nu^2) and 2 (1 - theta^2)(1 - nu^2) (printed with (1 - nu^2)^2).
+int error_constants(const char* name, double E, double nu, double theta, double tau12, double tau22,
+                    bool scheme, double* out) {
+    if (!out) return fail(LBM_ERR_ARG, std::string(name) + ": null output");
     if (theta == 0.0) theta = 1.0 / 3.0;
     if (tau12 == 0.0) tau12 = 0.5;
     if (tau22 == 0.0) tau22 = 0.5;
     if (!(E > 0.0) || !(nu > -1.0 && nu < 1.0) || !(theta > 0.0 && theta < 1.0))
-        return fail(LBM_ERR_ARG, "lbm_error_constants: need E > 0, -1 < nu < 1, 0 < theta < 1");
-    // Appendix B as printed (tau_21 = tau_12).
+        return fail(LBM_ERR_ARG, std::string(name) + ": need E > 0, -1 < nu < 1, 0 < theta < 1");
     const double th = theta, t12 = tau12, t21 = tau12, t22 = tau22;
     const double c = 1.0 - th * th, d = 1.0 - nu * nu, E2 = E * E, E3 = E2 * E;
     const double q = th * th * (1.0 + nu) + nu - 2.0 * th - 1.0;
@@ -619,7 +626,8 @@ int lbm_error_constants(double E, double nu, double theta, double tau12, double 
              th * (nu - th) * t12 / (c * d * d) * E2 +
              (-1.0 + th * th + 12.0 * th * (th - nu) * t12 * t22) / (12.0 * c * d) * E;
     out[1] = ((1.0 - nu) * (1.0 - nu) * (1.0 - nu) + 4.0 * th * (nu * nu * nu - nu * nu + 3.0 * nu + 1.0) +
-              th * th * (5.0 * nu * nu * nu - 15.0 * nu * nu - nu - 5.0)) / (8.0 * c * d * d * d) * E3 +
+              th * th * (5.0 * nu * nu * nu - 15.0 * nu * nu - nu - 5.0)) /
+                 ((scheme ? 8.0 * th : 8.0) * c * d * d * d) * E3 +
              (2.0 * th * ((1.0 - nu) * nu + th * th * (1.0 + nu) - th * (1.0 + nu * nu)) * t12 +
               (1.0 - th) * (1.0 - nu) * (1.0 + 2.0 * th - nu - th * th * (1.0 + nu)) * t21) /
                  (-4.0 * th * c * d * d) * E2 +
@@ -641,11 +649,44 @@ int lbm_error_constants(double E, double nu, double theta, double tau12, double 
              th * t22 / 4.0;
     out[4] = E3 / (8.0 * th * (1.0 + nu) * (1.0 + nu) * (1.0 + nu)) -
              (1.0 - th) * t12 / (4.0 * th * (1.0 + nu) * (1.0 + nu)) * E2 - (3.0 * th - 2.0) / (24.0 * (1.0 + nu)) * E;
-    out[5] = (nu * nu - 2.0 * th * nu + 1.0) / (c * d * d) * E2 + th * (nu - th) * t12 / (c * d * d) * E - 0.25;
+    const double dE = scheme ? d : d * d;   // denominator of the E terms of D1, D2 (besides 1 - theta^2)
+    out[5] = (nu * nu - 2.0 * th * nu + 1.0) / (c * d * d) * E2 + th * (nu - th) * t12 / (c * dE) * E - 0.25;
     out[6] = ((1.0 - nu) * (1.0 - nu) + 8.0 * th * nu - th * th * (5.0 * nu * nu - 2.0 * nu + 5.0)) /
                  (4.0 * th * c * d * d) * E2 -
-             q * t21 / (2.0 * c * d * d) * E - th / 2.0;
+             q * t21 / (2.0 * c * dE) * E - th / 2.0;
     out[7] = E2 / (4.0 * th * (1.0 + nu) * (1.0 + nu)) + t12 / (2.0 * (1.0 + nu)) * E - th / 4.0;
+    return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_error_constants(double E, double nu, double theta, double tau12, double tau22, double* out) {
+    return error_constants("lbm_error_constants", E, nu, theta, tau12, tau22, false, out);
+}
+
+int lbm_error_constants_scheme(double E, double nu, double theta, double tau12, double tau22, double* out) {
+    return error_constants("lbm_error_constants_scheme", E, nu, theta, tau12, tau22, true, out);
+}
+
+int lbm_fourth_order_taus(double E, double nu, double theta, double* tau12, double* tau22) {
+    if (!tau12 || !tau22) return fail(LBM_ERR_ARG, "lbm_fourth_order_taus: null output");
+    if (theta == 0.0) theta = 1.0 / 3.0;
+    if (!(E > 0.0) || !(nu > -1.0 && nu < 1.0) || !(theta > 0.0 && theta < 1.0) || nu == theta)
+        return fail(LBM_ERR_ARG, "lbm_fourth_order_taus: need E > 0, -1 < nu < 1, 0 < theta < 1, nu != theta");
+    // shear modulus (2D relations) and tau_11 of Table 1 (theta tau_11 = mu)
+    const double th = theta, mu = E / (2.0 * (1.0 + nu));
+    const double t11 = mu / th;
+    // Appendix C's tau_12 = tau_21: zeroes C5
+    const double t12 = (2.0 - 3.0 * th + 12.0 * th * t11 * t11) / (12.0 * (1.0 - th) * t11);
+    // tau_22 from C1 = 0 (C1 of Appendix B, linear in tau_22)
+    const double c = 1.0 - th * th, d = 1.0 - nu * nu;
+    const double a3 = (nu * nu - 2.0 * th * nu + 1.0) / (c * d * d * d);
+    const double a2 = th * (nu - th) / (c * d * d);
+    const double t22 = (1.0 - th * th - 12.0 * c * d * (a3 * E * E + a2 * t12 * E)) / (12.0 * th * (th - nu) * t12);
+    if (!std::isfinite(t12) || !std::isfinite(t22))
+        return fail(LBM_ERR_ARG, "lbm_fourth_order_taus: no finite relaxation times for these parameters");
+    *tau12 = t12;
+    *tau22 = t22;
     return LBM_OK;
 }
 

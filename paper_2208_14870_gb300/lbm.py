@@ -68,6 +68,10 @@ _SIGS = {
                                        _c.c_double, _c.c_int, _c.c_int, _c.POINTER(_c.c_double)]),
     "lbm_error_constants": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double, _c.c_double,
                                        _c.c_double, _vp]),
+    "lbm_error_constants_scheme": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double, _c.c_double,
+                                              _c.c_double, _vp]),
+    "lbm_fourth_order_taus": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double,
+                                         _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "lbm_reset": (_c.c_int, [_vp]),
     "lbm_iterate": (_c.c_int, [_vp, _i64]),
     "lbm_iterate_checked": (_c.c_int, [_vp, _i64, _c.c_int, _vp]),
@@ -187,6 +191,22 @@ def lbm_error_constants(E: float, nu: float, theta: float = 0.0, tau12: float = 
     _check(_lib.lbm_error_constants(E, nu, theta, tau12, tau22, out.ctypes.data),
            "lbm_error_constants")
     return out
+
+
+def lbm_error_constants_scheme(E: float, nu: float, theta: float = 0.0, tau12: float = 0.0,
+                               tau22: float = 0.0) -> np.ndarray:
+    """[C1..C5, D1..D3] of the scheme (Appendix B with three misprints read)."""
+    out = np.zeros(8)
+    _check(_lib.lbm_error_constants_scheme(E, nu, theta, tau12, tau22, out.ctypes.data),
+           "lbm_error_constants_scheme")
+    return out
+
+
+def lbm_fourth_order_taus(E: float, nu: float, theta: float = 0.0) -> tuple[float, float]:
+    """(tau12, tau22) zeroing C5 and C1 (fourth-order special case)."""
+    t12, t22 = _c.c_double(), _c.c_double()
+    _check(_lib.lbm_fourth_order_taus(E, nu, theta, _c.byref(t12), _c.byref(t22)), "lbm_fourth_order_taus")
+    return t12.value, t22.value
 
 
 def lbm_spectral_radius(lam: float, mu: float, theta: float = 0.0, tau12: float = 0.0,

@@ -7,8 +7,7 @@ Tolerances:
   * FP32 / FP16-shifted storage: the steady-state error against the FP64
     fixed point, relative to the field's maximum, must stay below the bound
     derived from the storage precision (FP32: 2e-5; FP16S: 2e-3 for
-    displacement and stress) -- see the per-dtype error table in the design
-    notes; the measured errors are printed.
+    displacement and stress); the measured errors are printed.
 """
 import numpy as np
 import pytest
