@@ -1,6 +1,7 @@
 """Host check of the wavefront schedule of k_wave (no GPU): the kernel's level
-windows, its two-row lag between step levels and its four-row shared-memory
-rings, replayed block by block in numpy on a toy per-node update with the
+windows, its two-row lag between step levels, its four-row shared-memory
+rings and its register history of the force (level j reads the entry
+2(j - 1) rows back), replayed block by block in numpy on a toy per-node update with the
 same pull streaming, must give exactly T single steps -- every ring read
 finds the row it needs, every slot index stays inside its ring row, every
 output node is written once, and the periodic wrap of slot coordinates stays
@@ -63,13 +64,16 @@ def _wave(state, gx, gy, T, seg, W, D):
         ring = np.full((T - 1, 8, D, W), np.nan)
         held = np.full((T - 1, D), -10 ** 9)          # lattice row held by each ring slot
         ybeg = y0 - (T - 1)
+        hist = [None] * (2 * (T - 1) + 1)              # force rows held in registers
         for i in range(rows + 3 * (T - 1)):
             writes = []                                # applied after the block barrier
             reads = set()                              # ring slots read in this iteration
+            hist = [ybeg + i if i < rows + 2 * (T - 1) else None] + hist[:-1]
             for tau in range(T, 1, -1):
                 if i < 3 * (tau - 1) or i > rows + 2 * T + tau - 4:
                     continue
                 yl = ybeg + i - 2 * (tau - 1)
+                assert hist[2 * (tau - 1)] == yl       # the register history holds this row's force
                 act = store_ok if tau == T else (t >= tau - 1) & (t <= W - tau)
                 for dy in (-1, 0, 1):
                     assert held[tau - 2][(yl + dy) % D] == yl + dy
