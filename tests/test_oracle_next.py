@@ -152,6 +152,71 @@ def test_printed_constants_against_the_scheme(E, nu, th, t12, t22):
         assert _close(pr[5], ex[5], scale) and _close(pr[6], ex[6], scale)
 
 
+@pytest.mark.parametrize("E,nu,th,t12,t22", EXTRACT_CASES[::2])
+def test_extracted_constants_predict_another_angle(E, nu, th, t12, t22):
+    """Out-of-sample check of Eq. ux_order2's structure: the constants
+    extracted at phi = 0, 45 degrees and atan(1/2) predict, at tan(phi) = 1/3,
+    the O(k^4) decay rates and O(k^2) displacement tilts of free plane waves and
+    the O(k^4) steady-state error under a force, as computed from the one-step
+    operator directly."""
+    ex, _ = oracle.leading_error_exact(E, nu, theta=th, tau12=t12, tau22=t22)
+    C1, C2, C3, C4, C5, D1, D2, D3 = ex
+    lam, mu = oracle.lame_2d(E, nu)
+    K = lam + mu
+    rates = oracle.relaxation_rates(lam, mu, theta=th, tau12=t12, tau22=t22)
+    phi = np.arctan(1.0 / 3.0)
+    c, s = np.cos(phi), np.sin(phi)
+    vL, vT = np.array([c, s]), np.array([-s, c])
+    Mm = F.moment_matrix()
+    sigma = -1.0
+
+    def measured(kap):
+        w, V = np.linalg.eig(F.amplification_matrix(rates, kap * c, kap * s))
+        out = {}
+        for j in np.argsort(-np.abs(w))[:2]:
+            U = Mm[:2] @ V[:, j]
+            kind = "L" if abs(np.vdot(vL, U)) > abs(np.vdot(vT, U)) else "T"
+            own, other = (vL, vT) if kind == "L" else (vT, vL)
+            s2 = (mu + K) if kind == "L" else mu
+            out[kind] = ((np.log(w[j]).real + s2 * kap ** 2) / kap ** 4,
+                         (np.vdot(other, U) / np.vdot(own, U)).real / kap ** 2)
+        return out
+
+    a, b = measured(0.01), measured(0.02)
+    got = {k: [(4 * a[k][i] - b[k][i]) / 3 for i in range(2)] for k in ("L", "T")}
+    c6s6, c2s2, g = c ** 6 + s ** 6, c * c * s * s, c * s * (c * c - s * s)
+    want = {"L": [sigma * (C1 * c6s6 + (C2 + C3 + C4 + C5) * c2s2), sigma * g * (C5 - C1 + C4) / (-K)],
+            "T": [sigma * (C5 * c6s6 + (C1 + C3 - C2 - C4) * c2s2), sigma * g * (C5 - C1 + C2) / K]}
+    scale = float(np.max(np.abs(ex)))
+    for k in ("L", "T"):
+        for i in range(2):
+            assert abs(got[k][i] - want[k][i]) <= 1e-4 * scale / (1.0 if i == 0 else min(K, mu)) + 1e-6, \
+                (k, i, got[k][i], want[k][i])
+
+    # steady state under a force: (U - U0) = sigma M^-1 (A - Dm M) U0 at O(k^4)
+    A = F.operator(rates)
+    Bx, By = F.force_vectors(rates)
+
+    def steady(kap):
+        kx, ky = kap * c, kap * s
+        Mk = np.array([[mu * kap ** 2 + K * kx * kx, K * kx * ky], [K * kx * ky, mu * kap ** 2 + K * ky * ky]])
+        S = F.shift_diag(kx, ky)
+        cols = []
+        for U0 in (np.array([1.0, 0.0]), np.array([0.0, 1.0])):
+            gh = Mk @ U0
+            fh = np.linalg.solve(np.eye(8) - S[:, None] * A, S * (Bx * gh[0] + By * gh[1]))
+            U = Mm[:2] @ fh + 0.5 * gh
+            cols.append(sigma * (Mk @ (U - U0)).real / kap ** 4)
+        return np.stack(cols, axis=1)
+
+    Q = (4 * steady(0.01) - steady(0.02)) / 3
+    Am = np.array([[C1 * c ** 4 + C3 * c2s2 + C5 * s ** 4, C2 * c ** 3 * s + C4 * c * s ** 3],
+                   [C2 * c * s ** 3 + C4 * c ** 3 * s, C1 * s ** 4 + C3 * c2s2 + C5 * c ** 4]])
+    Dm = np.array([[D1 * c * c + D3 * s * s, D2 * c * s], [D2 * c * s, D3 * c * c + D1 * s * s]])
+    Mh = np.array([[mu + K * c * c, K * c * s], [K * c * s, mu + K * s * s]])
+    assert np.max(np.abs(Q - (Am - Dm @ Mh))) <= 1e-4 * scale + 1e-6
+
+
 def test_exact_leading_error_matches_axis_modes():
     """The general extraction agrees with the axis-mode steady states of
     leading_error_axis (one lattice of 2048^2, not extrapolated: agreement to
