@@ -308,13 +308,20 @@ def plan_plain(m, spl, wave=False):
     return sizes + [1] * m
 
 
+def check_launch_steps(w, spl, wave=False):
+    """Steps of the launch that ends a residual window of w steps: a four-step
+    wavefront launch (check on its last level) where the schedule runs four
+    steps per launch, else a launch of at most two steps."""
+    return 4 if (wave and spl >= 4 and w >= 4) else min(spl, 2, w)
+
+
 def launches_per_iterate(iters, check_every, spl, wave=False):
     """Stream-collide launches of lbm_iterate_checked(iters, check_every) from
     step 0: each window is check_every - 1 plain steps grouped into launches of
     spl steps (the remainder in shorter ones) and ends with the check step,
-    the last step of a launch of min(spl, 2, check_every) steps."""
+    the last step of the window's last launch (check_launch_steps)."""
     def window(w):
-        last = min(spl, 2, w)       # checks ride on launches of at most two steps
+        last = check_launch_steps(w, spl, wave)
         return len(plan_plain(w - last, spl, wave)) + 1
     total, left = 0, iters
     while left >= check_every:
@@ -401,7 +408,7 @@ def dominant_block(check_every, spl, wave=False):
     runs as whole plain launches of k steps each, k the longest launch of the
     window (lbm_iterate_checked plans the window's check_every - 1 plain steps
     so; see plan_plain)."""
-    sizes = plan_plain(check_every - min(spl, 2, check_every), spl, wave)
+    sizes = plan_plain(check_every - check_launch_steps(check_every, spl, wave), spl, wave)
     if not sizes:
         return 0, spl
     big = sizes[0]

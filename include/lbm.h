@@ -431,13 +431,15 @@ int lbm_server_stats(lbm_server *srv, lbm_stats *out);
  *  f_src     device, 8 planes of nx*ny values of the storage type, plane
  *            stride nx*ny, population order of this header: the stored state,
  *            i.e. the post-collision populations f*_i(x) of the previous step
- *            (all zeros is the zero state of Eq. init_cond).
+ *            (all zeros is the zero state).
  *  f_dst     device, same layout, receives the state after the step; must not
  *            alias f_src.
  *  gx, gy    device, nx*ny values of the storage type (lattice force).
- *  snapshot  device, 2 planes of nx*ny values of the storage type: u_x, u_y
- *            of the previous check on input (zeros before the first); on
- *            output the displacement of this step's input state.
+ *  snapshot  device, 2 planes of nx*ny entries of 8 bytes each: u_x, u_y of
+ *            the previous check on input (zeros before the first); on output
+ *            the displacement of this step's input state.  LBM_F64: doubles;
+ *            LBM_F32: (hi, lo) pairs of floats whose sum is the displacement
+ *            to about 2^-44 relative (the layout lbm_iterate_checked keeps).
  *  result    device, 5 doubles: max|du|, max|u|, sum du^2, sum u^2 and a
  *            non-finite flag, du being the change of u since the snapshot;
  *            r_inf = result[0] / (k * result[1]) for a window of k steps.

@@ -9,7 +9,7 @@ namespace cg = cooperative_groups;
 
 template <int S, int V, bool CHECK>
 __device__ __forceinline__ void arena_tile(const BatchArgs& A, const BatchProb& P, int tile,
-                                           int s, float acc[kRes]) {
+                                           int s, ResAcc<S>& acc) {
     StepParams a{};
     const int64_t n = (int64_t)P.nx * P.ny;
     a.nx = P.nx;
@@ -43,30 +43,27 @@ __device__ __forceinline__ void arena_tile(const BatchArgs& A, const BatchProb& 
     step_tile<S, V, false, CHECK>(a, c, tx, ty, acc);
 }
 
-// Block reduction of one tile's residual partials into the problem's FP64
-// accumulator (maxima through the bit patterns of non-negative doubles).
-__device__ __forceinline__ void tile_to_problem(float acc[kRes], double* dst,
-                                                float (&red)[kRes][kThreads / 32]) {
+// Block reduction of one tile's residual partials (converted to FP64 per
+// thread) into the problem's FP64 accumulator (maxima through the bit
+// patterns of non-negative doubles).
+template <int S>
+__device__ __forceinline__ void tile_to_problem(const ResAcc<S>& acc, double* dst,
+                                                double (&red)[kRes][kThreads / 32]) {
     const int tid = threadIdx.y * 32 + threadIdx.x, lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        acc[0] = fmaxf(acc[0], __shfl_xor_sync(0xffffffffu, acc[0], o));
-        acc[1] = fmaxf(acc[1], __shfl_xor_sync(0xffffffffu, acc[1], o));
-        acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
-        acc[3] += __shfl_xor_sync(0xffffffffu, acc[3], o);
-        acc[4] = fmaxf(acc[4], __shfl_xor_sync(0xffffffffu, acc[4], o));
-    }
+    double v[kRes];
+    res_to_double<S>(acc, v);
+    warp_reduce_res(v);
     if (lane == 0)
-        for (int k = 0; k < kRes; ++k) red[k][warp] = acc[k];
+        for (int k = 0; k < kRes; ++k) red[k][warp] = v[k];
     __syncthreads();
     if (tid == 0) {
         double m0 = 0.0, m1 = 0.0, s2 = 0.0, s3 = 0.0, b = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) {
-            m0 = fmax(m0, (double)red[0][w]);
-            m1 = fmax(m1, (double)red[1][w]);
-            s2 += (double)red[2][w];
-            s3 += (double)red[3][w];
-            b = fmax(b, (double)red[4][w]);
+            m0 = fmax(m0, red[0][w]);
+            m1 = fmax(m1, red[1][w]);
+            s2 += red[2][w];
+            s3 += red[3][w];
+            b = fmax(b, red[4][w]);
         }
         unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
         atomicMax(d + 0, (unsigned long long)__double_as_longlong(m0));
@@ -81,7 +78,7 @@ __device__ __forceinline__ void tile_to_problem(float acc[kRes], double* dst,
 template <int S, int V>
 __global__ void __launch_bounds__(kThreads, 2) k_arena_chunk(const BatchArgs A) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ float red[kRes][kThreads / 32];
+    __shared__ double red[kRes][kThreads / 32];
     const int ntiles = *A.ntiles;
     for (int s = 0; s < A.nsteps; ++s) {
         const bool last = (s == A.nsteps - 1);
@@ -89,12 +86,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_arena_chunk(const BatchArgs A) 
             const uint2 tl = A.tiles[t];
             const BatchProb P = A.probs[tl.x];
             const bool check = last && P.check;  // uniform over the block
-            float acc[kRes] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            ResAcc<S> acc;
             if (!check) {
                 arena_tile<S, V, false>(A, P, (int)tl.y, s, acc);
             } else {
                 arena_tile<S, V, true>(A, P, (int)tl.y, s, acc);
-                tile_to_problem(acc, A.acc + (int64_t)tl.x * kRes, red);
+                tile_to_problem<S>(acc, A.acc + (int64_t)tl.x * kRes, red);
             }
         }
         if (s + 1 < A.nsteps) grid.sync();
@@ -104,7 +101,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_arena_chunk(const BatchArgs A) 
 // One tile of two steps (k_step2's tile) of problem P; s counts step pairs.
 template <int S, bool CHECK>
 __device__ __forceinline__ void arena_tile2(const BatchArgs& A, const BatchProb& P, int tile, int s,
-                                            float* sm, float acc[kRes]) {
+                                            float* sm, ResAcc<S>& acc) {
     StepParams a{};
     const int64_t n = (int64_t)P.nx * P.ny;
     a.nx = P.nx;
@@ -141,7 +138,7 @@ template <int S>
 __global__ void __launch_bounds__(kT2Threads, 2) k_arena_chunk2(const BatchArgs A) {
     cg::grid_group grid = cg::this_grid();
     extern __shared__ float t2_smem[];
-    __shared__ float red[kRes][kThreads / 32];
+    __shared__ double red[kRes][kThreads / 32];
     const int ntiles = *A.ntiles;
     const int npairs = A.nsteps / 2;
     for (int s = 0; s < npairs; ++s) {
@@ -150,12 +147,12 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_arena_chunk2(const BatchArgs 
             const uint2 tl = A.tiles[t];
             const BatchProb P = A.probs[tl.x];
             const bool check = last && P.check;  // uniform over the block
-            float acc[kRes] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            ResAcc<S> acc;
             if (!check) {
                 arena_tile2<S, false>(A, P, (int)tl.y, s, t2_smem, acc);
             } else {
                 arena_tile2<S, true>(A, P, (int)tl.y, s, t2_smem, acc);
-                tile_to_problem(acc, A.acc + (int64_t)tl.x * kRes, red);
+                tile_to_problem<S>(acc, A.acc + (int64_t)tl.x * kRes, red);
             }
             __syncthreads();   // the slots are reused by the block's next tile
         }

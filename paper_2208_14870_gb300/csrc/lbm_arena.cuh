@@ -5,7 +5,8 @@
 // Every problem p owns, in three device buffers,
 //   pop[0], pop[1] : its 8 population planes (ping-pong; FP32 or FP16),
 //   car[0], car[1] : FP16-shifted only: the two FP32 carriers, one float2 per node,
-//   fs             : force (2 planes) then residual snapshot (2 planes), FP32,
+//   fs             : force (2 FP32 planes) then residual snapshot (2 planes of
+//                    (hi, lo) FP32 pairs),
 // placed by a first-fit allocator (256-byte aligned).  The work of one step
 // is the list of (problem, tile) pairs of the active problems; the kernel
 // walks that list grid-stride, then synchronises the whole grid before the

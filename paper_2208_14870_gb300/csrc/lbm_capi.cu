@@ -55,8 +55,9 @@ struct lbm_ctx {
     void* pop[2] = {nullptr, nullptr};
     float* car[2] = {nullptr, nullptr};
     void* force = nullptr;         // 2 planes of the storage force type
-    void* snap = nullptr;          // 2*n of the snapshot type
-    double* partials = nullptr;
+    void* snap = nullptr;          // residual snapshot: 2 planes of n entries of 8 bytes (ResSnap)
+    double* partials = nullptr;    // residual partial sets, kRes doubles each
+    int64_t partials_len = 0;      // partial sets the buffer holds
     double* result = nullptr;      // kRes doubles (device)
     unsigned long long* absmax = nullptr;
     unsigned int* bad = nullptr;
@@ -201,11 +202,31 @@ cudaError_t launch_multi(lbm_ctx* c, int T) {
     if (!(c->wave != 0 && wave_fits(c->nx, c->ny))) return T == 3 ? launch_step3(c) : cudaErrorInvalidValue;
     const StepParams a = params(c, c->cur);
     const int seg = wave_seg(c, T);
-    cudaError_t e = c->dtype == LBM_F32 ? wave_f32(a, coef<float>(c->rates), c->gen, T, seg, c->stream)
-                                        : wave_f16s(a, coef<float>(c->rates), c->gen, T, seg, c->stream);
+    cudaError_t e = c->dtype == LBM_F32 ? wave_f32(a, coef<float>(c->rates), c->gen, T, false, seg, c->stream)
+                                        : wave_f16s(a, coef<float>(c->rates), c->gen, T, false, seg, c->stream);
     if (e == cudaSuccess) {
         c->cur ^= 1;
         c->step += T;
+        c->staged_fields = false;
+    }
+    return e;
+}
+
+int ensure_partials(lbm_ctx* c, int64_t sets);
+
+// Four steps on the wavefront schedule whose last step carries the residual
+// check (one partial set per block, combined by k_residual_finish).
+cudaError_t launch_wave_checked(lbm_ctx* c) {
+    const int seg = wave_seg(c, 4);
+    const int64_t blocks = wave_blocks<4>(c->nx, c->ny, seg);
+    if (ensure_partials(c, blocks) != LBM_OK) return cudaErrorMemoryAllocation;
+    const StepParams a = params(c, c->cur);
+    cudaError_t e = c->dtype == LBM_F32 ? wave_f32(a, coef<float>(c->rates), c->gen, 4, true, seg, c->stream)
+                                        : wave_f16s(a, coef<float>(c->rates), c->gen, 4, true, seg, c->stream);
+    if (e == cudaSuccess) e = finish_residual_launch(c, blocks);
+    if (e == cudaSuccess) {
+        c->cur ^= 1;
+        c->step += 4;
         c->staged_fields = false;
     }
     return e;
@@ -239,11 +260,16 @@ cudaError_t run_plain(lbm_ctx* c, int64_t n) {
 }
 
 // to_check - 1 plain steps followed by the residual-check step (the last
-// step of the last launch).  With three steps per launch the check still
-// rides on a two-step launch: a three-step launch with the check costs twice
-// a plain one, a two-step launch with the check 1.3 times.
+// step of the last launch).  On the four-step wavefront schedule the check is
+// the last level of a four-step launch; with three steps per launch on tiles
+// it rides on a two-step launch (a three-step tile launch with the check
+// costs twice a plain one, a two-step launch with the check 1.3 times).
 cudaError_t run_window(lbm_ctx* c, int64_t to_check) {
     cudaError_t e;
+    if (c->spl >= 4 && to_check >= 4 && c->wave != 0 && wave_fits(c->nx, c->ny)) {
+        e = run_plain(c, to_check - 4);
+        return e == cudaSuccess ? launch_wave_checked(c) : e;
+    }
     if (c->spl >= 2 && to_check >= 2) {
         e = run_plain(c, to_check - 2);
         return e == cudaSuccess ? launch_step2(c, true) : e;
@@ -290,6 +316,24 @@ int ensure_staging(lbm_ctx* c, int64_t len) {
     CK(cudaMalloc(&c->staging, len * sizeof(double)));
     c->staging_len = len;
     c->bytes += len * sizeof(double);
+    return LBM_OK;
+}
+
+// A partials buffer of at least `sets` partial sets (grown on demand: a
+// wavefront check launch with short segments may have more blocks than the
+// tile launches it was sized for).
+int ensure_partials(lbm_ctx* c, int64_t sets) {
+    if (c->partials_len >= sets) return LBM_OK;
+    if (c->partials) {
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaFree(c->partials));
+        c->bytes -= c->partials_len * kRes * sizeof(double);
+        c->partials = nullptr;
+        c->partials_len = 0;
+    }
+    CK(cudaMalloc((void**)&c->partials, sets * kRes * sizeof(double)));
+    c->partials_len = sets;
+    c->bytes += sets * kRes * sizeof(double);
     return LBM_OK;
 }
 
@@ -484,10 +528,13 @@ int lbm_create_ex(int nx, int ny, double lambda, double mu, int dtype, const lbm
         if (e == cudaSuccess && dtype == LBM_F16S) e = alloc((void**)&c->car[i], cb);
     }
     if (e == cudaSuccess) e = alloc(&c->force, fb);
-    const size_t snap_bytes = (dtype == LBM_F64 ? sizeof(double) : sizeof(float)) * 2 * c->n;
+    // FP64: two planes of doubles; FP32 / FP16S: two planes of (hi, lo) FP32 pairs
+    const size_t snap_bytes = 16 * (size_t)c->n;
     if (e == cudaSuccess) e = alloc(&c->snap, snap_bytes);
-    if (e == cudaSuccess) e = alloc((void**)&c->partials,
-                                       sizeof(double) * kRes * std::max(c->nblocks, c->nblocks2));
+    c->partials_len = std::max(c->nblocks, c->nblocks2);
+    if (dtype != LBM_F64 && wave_fits(nx, ny))
+        c->partials_len = std::max(c->partials_len, wave_blocks<4>(nx, ny, wave_seg(c, 4)));
+    if (e == cudaSuccess) e = alloc((void**)&c->partials, sizeof(double) * kRes * c->partials_len);
     if (e == cudaSuccess) e = alloc((void**)&c->result, sizeof(double) * kRes);
     if (e == cudaSuccess) e = alloc((void**)&c->absmax, sizeof(unsigned long long));
     if (e == cudaSuccess) e = alloc((void**)&c->bad, sizeof(unsigned int));

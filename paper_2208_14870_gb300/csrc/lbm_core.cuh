@@ -160,6 +160,55 @@ __device__ __forceinline__ Mom<T> deviation_moments(const Mom<T>& s, T qtheta) {
     return n;
 }
 
+// Error-free FP32 transformations for the steady-state residual.  GB300's
+// FP64 pipe issues about 1/64 of the FP32 rate, so the residual of FP32 and
+// FP16-shifted storage evaluates the displacement in FP32 pairs (hi + lo)
+// instead of FP64 per node: two_sum is Knuth's TwoSum (s + e == a + b
+// exactly, six FP32 additions, no branch), fast_two_sum Dekker's form for
+// |a| >= |b| (three additions).  Every operation is written with explicit
+// rounding so that no compiler contraction or reassociation can touch it.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+__device__ __forceinline__ float fast_two_sum(float a, float b, float& e) {
+    const float s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+    return s;
+}
+
+// The displacement of eight FP32 pre-collision populations, u = mbar_10 =
+// m_10 + g_x / 2 and v = mbar_01 (Eqs. coll10, coll01; Table 2), as FP32
+// pairs (u_hi, u_lo, v_hi, v_lo).  The sums are the moment butterfly's
+// (moments(), then collide's half force), so u_hi + u_lo carries exactly the
+// value the butterfly rounds, with each addition's rounding error recovered
+// by two_sum: m_12 = r - s with r = f5 - f7, s = f6 - f8, m_10 = (f1 - f3) +
+// m_12, u = m_10 + g_x / 2 (and m_21 = r + s, m_01 = (f2 - f4) + m_21).  The
+// error terms are summed in FP32, so the pair is exact to about 2^-44 of the
+// largest partial sum; the hi parts are the FP32 values the collision uses.
+__device__ __forceinline__ float4 exact_displacement(const float f[8], float gx, float gy) {
+    float er, es, e12, e21, ea, eb, e10, e01, eu, ev;
+    const float r = two_sum(f[4], -f[6], er);
+    const float s = two_sum(f[5], -f[7], es);
+    const float m12 = two_sum(r, -s, e12);
+    const float m21 = two_sum(r, s, e21);
+    const float a = two_sum(f[0], -f[2], ea);
+    const float b = two_sum(f[1], -f[3], eb);
+    const float m10 = two_sum(a, m12, e10);
+    const float m01 = two_sum(b, m21, e01);
+    const float u = two_sum(m10, 0.5f * gx, eu);
+    const float v = two_sum(m01, 0.5f * gy, ev);
+    const float ulo = __fadd_rn(__fadd_rn(__fadd_rn(eu, e10), __fadd_rn(ea, e12)), __fsub_rn(er, es));
+    const float vlo = __fadd_rn(__fadd_rn(__fadd_rn(ev, e01), __fadd_rn(eb, e21)), __fadd_rn(er, es));
+    float4 d;
+    d.x = two_sum(u, ulo, d.y);
+    d.z = two_sum(v, vlo, d.w);
+    return d;
+}
+
 __device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 __device__ __forceinline__ int wrap_inc(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 

@@ -30,7 +30,8 @@ int cuerr(cudaError_t e, const char* what, std::string* err) {
 
 int64_t pop_bytes_per_node(int dtype) { return dtype == S_F16S ? 8 * 2 : 8 * 4; }
 int64_t car_bytes_per_node(int dtype) { return dtype == S_F16S ? 2 * 4 : 0; }
-constexpr int64_t kFsBytesPerNode = 4 * 4;  // force (2) + snapshot (2), FP32
+// force (2 FP32 planes) + residual snapshot (2 planes of (hi, lo) FP32 pairs)
+constexpr int64_t kFsBytesPerNode = 2 * 4 + 2 * 8;
 
 }  // namespace
 
@@ -165,7 +166,7 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
         h_force_[n + i] = (float)b;
     }
     ECK(cudaMemcpyAsync(fs_ + p.fs_off, h_force_, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, st_));
-    ECK(cudaMemsetAsync(fs_ + p.fs_off + sizeof(float) * 2 * n, 0, sizeof(float) * 2 * n, st_));
+    ECK(cudaMemsetAsync(fs_ + p.fs_off + sizeof(float) * 2 * n, 0, sizeof(float2) * 2 * n, st_));
     ECK(cudaMemsetAsync(pop_[0] + p.pop_off, 0, p.pop_bytes, st_));
     if (dtype_ == S_F16S) ECK(cudaMemsetAsync(car_[0] + p.car_off, 0, p.car_bytes, st_));
     p.parity = 0;

@@ -16,6 +16,8 @@
 // load or store instruction touches 32 consecutive nodes of one plane.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_core.cuh"
 
 namespace lbm {
@@ -51,11 +53,10 @@ constexpr int max_vec() {
 constexpr int kThreads = 32 * BY;
 
 template <int S> struct StoreT;
-// T: collision arithmetic, P: stored population, G: stored force,
-// U: displacement snapshot of the residual check (the type u is computed in).
-template <> struct StoreT<S_F64> { using T = double; using P = double; using G = double; using U = double; };
-template <> struct StoreT<S_F32> { using T = float; using P = float; using G = float; using U = float; };
-template <> struct StoreT<S_F16S> { using T = float; using P = __half; using G = float; using U = float; };
+// T: collision arithmetic, P: stored population, G: stored force.
+template <> struct StoreT<S_F64> { using T = double; using P = double; using G = double; };
+template <> struct StoreT<S_F32> { using T = float; using P = float; using G = float; };
+template <> struct StoreT<S_F16S> { using T = float; using P = __half; using G = float; };
 
 // Residual partial sums of one block: max|du|, max|u|, sum du^2, sum u^2,
 // non-finite flag.
@@ -72,7 +73,7 @@ struct StepParams {
     const void* gy;
     float hscale;           // F16S: stored = deviation * hscale (power of two)
     float hinv;             // 1 / hscale
-    void* snap;             // residual: u_x, u_y snapshot, 2 planes of nx*ny (type U)
+    void* snap;             // residual: u_x, u_y snapshot, 2 planes of nx*ny (ResSnap)
     double* partials;       // residual: kRes doubles per block
     unsigned int* counter;  // residual: blocks finished, reset by the last block; null:
                             // blocks only write partials (k_residual_finish combines them)
@@ -82,6 +83,142 @@ struct StepParams {
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// ---------------------------------------------------------------------------
+// Steady-state residual (Sec. 2.1's stopping test; reading: max and L2 norms
+// of u^t - u^(t-w) over a window of w steps).  Each thread keeps partials over
+// its nodes -- max|du|, max|u| (over nodes and both components), sum du^2,
+// sum u^2 and a non-finite flag -- and the snapshot holds u of the previous
+// check, two planes of nx*ny entries:
+//   FP64 storage: u from the FP64 collision, FP64 snapshot and partials;
+//   FP32 / FP16S: u as an exact FP32 pair from exact_displacement, the
+//   snapshot as (hi, lo) pairs (16 bytes per node, like two FP64 planes), and
+//   pair partials (about 2^-44 relative), converted to FP64 per thread.
+// Warps, blocks and the grid combine the partials in FP64.
+template <int S> struct ResSnap { float2 u, v; };          // (hi, lo) per component
+template <> struct ResSnap<S_F64> { double u, v; };
+
+template <int S> struct ResAcc {
+    float dh = 0.f, dl = 0.f, uh = 0.f, ul = 0.f, d2h = 0.f, d2l = 0.f, u2h = 0.f, u2l = 0.f, bad = 0.f;
+};
+template <> struct ResAcc<S_F64> {
+    double d = 0.0, u = 0.0, d2 = 0.0, u2 = 0.0, bad = 0.0;
+};
+
+// max(m, |h + l|) on normalised pairs (|l| <= ulp(h) / 2), lexicographically.
+__device__ __forceinline__ void pair_max_abs(float& mh, float& ml, float h, float l) {
+    if (h < 0.0f) {
+        h = -h;
+        l = -l;
+    }
+    if (h > mh || (h == mh && l > ml)) {
+        mh = h;
+        ml = l;
+    }
+}
+
+// s += (h + l)^2 in pair arithmetic: h*h with its exact FMA error, plus
+// 2 h l (l^2 is below 2^-48 h^2 and dropped); the sum stays normalised.
+__device__ __forceinline__ void pair_add_square(float& sh, float& sl, float h, float l) {
+    const float p = __fmul_rn(h, h);
+    const float e = fmaf(2.0f * h, l, fmaf(h, h, -p));
+    float t;
+    const float s = two_sum(sh, p, t);
+    sh = fast_two_sum(s, __fadd_rn(sl, __fadd_rn(t, e)), sl);
+}
+
+template <int S>
+__device__ __forceinline__ ResSnap<S> snap_load(const StepParams& a, int64_t n, int64_t idx) {
+    ResSnap<S> o;
+    if constexpr (S == S_F64) {
+        const double* sp = static_cast<const double*>(a.snap);
+        o.u = sp[idx];
+        o.v = sp[n + idx];
+    } else {
+        const float2* sp = static_cast<const float2*>(a.snap);
+        o.u = sp[idx];
+        o.v = sp[n + idx];
+    }
+    return o;
+}
+
+// Residual check of one node: compare u^t of the step's input state (pulled
+// populations f, force g; FP64 storage: the collision's u, v) with the
+// snapshot entry `old` loaded before, store u^t as the new snapshot entry and
+// update the thread's partials.
+template <int S>
+__device__ __forceinline__ void check_node(const StepParams& a, int64_t n, int64_t idx, ResAcc<S>& acc,
+                                           const ResSnap<S>& old, const typename StoreT<S>::T f[8],
+                                           typename StoreT<S>::T gx, typename StoreT<S>::T gy,
+                                           typename StoreT<S>::T u, typename StoreT<S>::T v) {
+    if constexpr (S == S_F64) {
+        (void)f;
+        (void)gx;
+        (void)gy;
+        double* sp = static_cast<double*>(a.snap);
+        sp[idx] = u;
+        sp[n + idx] = v;
+        const double du = u - old.u, dv = v - old.v;
+        acc.d = fmax(acc.d, fmax(fabs(du), fabs(dv)));
+        acc.u = fmax(acc.u, fmax(fabs(u), fabs(v)));
+        acc.d2 += du * du + dv * dv;
+        acc.u2 += u * u + v * v;
+        if (!(isfinite(u) && isfinite(v))) acc.bad = 1.0;
+    } else {
+        (void)u;
+        (void)v;
+        const float4 w = exact_displacement(f, gx, gy);
+        float2* sp = static_cast<float2*>(a.snap);
+        sp[idx] = make_float2(w.x, w.y);
+        sp[n + idx] = make_float2(w.z, w.w);
+        float e, dl;
+        // du = u^t - u^(t-w) as a pair: the hi parts' difference exactly,
+        // then the lo parts' (both below an ulp of u)
+        float dh = two_sum(w.x, -old.u.x, e);
+        dh = two_sum(dh, __fadd_rn(e, __fsub_rn(w.y, old.u.y)), dl);
+        pair_max_abs(acc.dh, acc.dl, dh, dl);
+        pair_add_square(acc.d2h, acc.d2l, dh, dl);
+        dh = two_sum(w.z, -old.v.x, e);
+        dh = two_sum(dh, __fadd_rn(e, __fsub_rn(w.w, old.v.y)), dl);
+        pair_max_abs(acc.dh, acc.dl, dh, dl);
+        pair_add_square(acc.d2h, acc.d2l, dh, dl);
+        pair_max_abs(acc.uh, acc.ul, w.x, w.y);
+        pair_max_abs(acc.uh, acc.ul, w.z, w.w);
+        pair_add_square(acc.u2h, acc.u2l, w.x, w.y);
+        pair_add_square(acc.u2h, acc.u2l, w.z, w.w);
+        if (!(isfinite(w.x) && isfinite(w.z))) acc.bad = 1.0f;
+    }
+}
+
+// The thread's partials in FP64: [max|du|, max|u|, sum du^2, sum u^2, flag].
+template <int S>
+__device__ __forceinline__ void res_to_double(const ResAcc<S>& acc, double w[kRes]) {
+    if constexpr (S == S_F64) {
+        w[0] = acc.d;
+        w[1] = acc.u;
+        w[2] = acc.d2;
+        w[3] = acc.u2;
+        w[4] = acc.bad;
+    } else {
+        w[0] = (double)acc.dh + (double)acc.dl;
+        w[1] = (double)acc.uh + (double)acc.ul;
+        w[2] = (double)acc.d2h + (double)acc.d2l;
+        w[3] = (double)acc.u2h + (double)acc.u2l;
+        w[4] = acc.bad;
+    }
+}
+
+// Warp-level FP64 combination of kRes partials (result in every lane).
+__device__ __forceinline__ void warp_reduce_res(double w[kRes]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        w[0] = fmax(w[0], __shfl_xor_sync(0xffffffffu, w[0], o));
+        w[1] = fmax(w[1], __shfl_xor_sync(0xffffffffu, w[1], o));
+        w[2] += __shfl_xor_sync(0xffffffffu, w[2], o);
+        w[3] += __shfl_xor_sync(0xffffffffu, w[3], o);
+        w[4] = fmax(w[4], __shfl_xor_sync(0xffffffffu, w[4], o));
+    }
+}
+
 // Stored values that the pull of one node reads: the 8 populations f*_p(x - c_p)
 // as stored (and, FP16S, the carriers of the 8 source nodes).
 template <int S> struct Pulled { typename StoreT<S>::P p[8]; };
@@ -89,14 +226,15 @@ template <> struct Pulled<S_F16S> { __half p[8]; float2 c[8]; };
 
 // Load the stored values of the pull of node (x, y) (loads only).
 // r0, rm, rp: offsets of rows y, y-1, y+1 (wrapped); xm, xp: columns x-1, x+1.
-template <int S>
-__device__ __forceinline__ void pull_load(const StepParams& a, int64_t r0, int64_t rm, int64_t rp,
+// I: in-plane offset type (int where a plane has fewer than 2^31 nodes).
+template <int S, typename I = int64_t>
+__device__ __forceinline__ void pull_load(const StepParams& a, I r0, I rm, I rp,
                                           int x, int xm, int xp, Pulled<S>& q) {
     using P = typename StoreT<S>::P;
     const P* s = static_cast<const P*>(a.src);
     const int64_t pl = a.plane;
-    const int64_t i0 = r0 + xm, i1 = rm + x, i2 = r0 + xp, i3 = rp + x;
-    const int64_t i4 = rm + xm, i5 = rm + xp, i6 = rp + xp, i7 = rp + xm;
+    const I i0 = r0 + xm, i1 = rm + x, i2 = r0 + xp, i3 = rp + x;
+    const I i4 = rm + xm, i5 = rm + xp, i6 = rp + xp, i7 = rp + xm;
     if constexpr (S == S_F16S) {
         // carriers interleaved per node: (m*_10, m*_01) as one float2
         const float2* c = reinterpret_cast<const float2*>(a.csrc);
@@ -200,51 +338,28 @@ __device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
     }
 }
 
-// Residual reduction.  Each thread holds partials over its V nodes in the
-// snapshot type U (max|du|, max|u|, sum du^2, sum u^2, non-finite flag); a
-// warp combines them in U (maxima are exact; FP32 sums of at most 32*V terms
-// carry a relative error below 1e-6), then the block and the grid combine
-// the warp results in FP64.  With a counter, the grid-level pass is done by
-// the last block to finish (counted with an atomic), which also resets the
-// counter for the next check; without one (the library's own check launches)
-// the blocks stop after writing their partials and k_residual_finish combines
-// them in a separate launch.
-template <typename U>
-__device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) {
+// Residual reduction of a block.  Each thread's partials (ResAcc) are
+// converted to FP64 and combined across the warp, the block and the grid in
+// FP64.  With a counter, the grid-level pass is done by the last block to
+// finish (counted with an atomic), which also resets the counter for the next
+// check; without one (the library's own check launches) the blocks stop after
+// writing their partials and k_residual_finish combines them in a separate
+// launch.
+template <int S>
+__device__ __forceinline__ void residual_reduce(const StepParams& a, const ResAcc<S>& acc) {
     __shared__ double sh[kRes][kThreads / 32];
     __shared__ bool is_last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int nwarps = (blockDim.x * blockDim.y) >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v[0] = max(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
-        v[1] = max(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
-        v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
-        v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
-        v[4] = max(v[4], __shfl_xor_sync(0xffffffffu, v[4], o));
-    }
+    double v[kRes];
+    res_to_double<S>(acc, v);
+    warp_reduce_res(v);
     if (lane == 0)
-        for (int k = 0; k < kRes; ++k) sh[k][warp] = double(v[k]);
+        for (int k = 0; k < kRes; ++k) sh[k][warp] = v[k];
     __syncthreads();
     const unsigned int nblocks = gridDim.x * gridDim.y;
     const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
-    if (a.counter == nullptr) {
-        // Partials only: a later k_residual_finish launch combines them, so
-        // the block ends here without a memory fence or a grid counter.
-        if (tid == 0) {
-            double w[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
-            for (int i = 0; i < nwarps; ++i) {
-                w[0] = fmax(w[0], sh[0][i]);
-                w[1] = fmax(w[1], sh[1][i]);
-                w[2] += sh[2][i];
-                w[3] += sh[3][i];
-                w[4] = fmax(w[4], sh[4][i]);
-            }
-            for (int k = 0; k < kRes; ++k) a.partials[(int64_t)bid * kRes + k] = w[k];
-        }
-        return;
-    }
     if (tid == 0) {
         double w[kRes] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int i = 0; i < nwarps; ++i) {
@@ -255,10 +370,15 @@ __device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) 
             w[4] = fmax(w[4], sh[4][i]);
         }
         for (int k = 0; k < kRes; ++k) a.partials[(int64_t)bid * kRes + k] = w[k];
-        __threadfence();
-        const unsigned int done = atomicAdd(a.counter, 1u);
-        is_last = (done == nblocks - 1);
+        if (a.counter != nullptr) {
+            __threadfence();
+            const unsigned int done = atomicAdd(a.counter, 1u);
+            is_last = (done == nblocks - 1);
+        }
     }
+    // Partials only: a later k_residual_finish launch combines them, so the
+    // block ends here without a memory fence or a grid counter.
+    if (a.counter == nullptr) return;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
@@ -289,14 +409,7 @@ __device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) 
         w[3] += __ldcg(p + 3);
         w[4] = fmax(w[4], __ldcg(p + 4));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        w[0] = fmax(w[0], __shfl_xor_sync(0xffffffffu, w[0], o));
-        w[1] = fmax(w[1], __shfl_xor_sync(0xffffffffu, w[1], o));
-        w[2] += __shfl_xor_sync(0xffffffffu, w[2], o);
-        w[3] += __shfl_xor_sync(0xffffffffu, w[3], o);
-        w[4] = fmax(w[4], __shfl_xor_sync(0xffffffffu, w[4], o));
-    }
+    warp_reduce_res(w);
     __syncthreads();
     if (lane == 0)
         for (int k = 0; k < kRes; ++k) sh[k][warp] = w[k];
@@ -328,28 +441,26 @@ __device__ __forceinline__ void residual_reduce(const StepParams& a, U v[kRes]) 
 // kMaxCheckBlocks blocks (more tiles per block beyond that).
 // One tile of one step: tile (tx, ty) covers columns tx*32V .. tx*32V+32V-1
 // and rows ty*BY .. ty*BY+BY-1.  With CHECK the thread's residual partials
-// are accumulated into acc (snapshot type U).
+// are accumulated into acc.
 template <int S, int V, bool GEN, bool CHECK>
 __device__ __forceinline__ void step_tile(const StepParams& a,
                                           const Coef<typename StoreT<S>::T>& c, int tx, int ty,
-                                          typename StoreT<S>::U acc[kRes]) {
+                                          ResAcc<S>& acc) {
     using T = typename StoreT<S>::T;
     using G = typename StoreT<S>::G;
-    using U = typename StoreT<S>::U;
     const int nx = a.nx, ny = a.ny;
     const int y = ty * BY + threadIdx.y;
     const int xb = tx * (32 * V) + threadIdx.x;
     if (y >= ny) return;
     const G* __restrict__ gxp = static_cast<const G*>(a.gx);
     const G* __restrict__ gyp = static_cast<const G*>(a.gy);
-    U* __restrict__ snap = static_cast<U*>(a.snap);
     const int64_t n = (int64_t)nx * ny;
     const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
     const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
     // Phase 1: issue every load of the thread's V nodes before any store,
     // so that up to V*10 (V*12 with the snapshot) loads are in flight.
     T f[V][8], gx[V], gy[V];
-    U so[V][2];
+    ResSnap<S> so[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) {
         const int x = xb + 32 * j;
@@ -357,10 +468,7 @@ __device__ __forceinline__ void step_tile(const StepParams& a,
             gather<S>(a, r0, rm, rp, x, wrap_dec(x, nx), wrap_inc(x, nx), f[j], c.theta);
             gx[j] = T(ldg(gxp + r0 + x));
             gy[j] = T(ldg(gyp + r0 + x));
-            if (CHECK) {
-                so[j][0] = snap[r0 + x];
-                so[j][1] = snap[n + r0 + x];
-            }
+            if (CHECK) so[j] = snap_load<S>(a, n, r0 + x);
         }
     }
     // Phase 2: collide and store.
@@ -372,17 +480,7 @@ __device__ __forceinline__ void step_tile(const StepParams& a,
             T u, v;
             const Mom<T> s = collide<T, GEN>(moments(f[j]), gx[j], gy[j], c, u, v);
             scatter_local<S>(a, idx, s, c.qtheta);
-            if (CHECK) {
-                const U uu = U(u), vv = U(v);
-                snap[idx] = uu;
-                snap[n + idx] = vv;
-                const U du = uu - so[j][0], dv = vv - so[j][1];
-                acc[0] = max(acc[0], max(abs(du), abs(dv)));
-                acc[1] = max(acc[1], max(abs(uu), abs(vv)));
-                acc[2] += du * du + dv * dv;
-                acc[3] += uu * uu + vv * vv;
-                if (!(isfinite(uu) && isfinite(vv))) acc[4] = U(1);
-            }
+            if (CHECK) check_node<S>(a, n, idx, acc, so[j], f[j], gx[j], gy[j], u, v);
         }
     }
 }
@@ -390,15 +488,14 @@ __device__ __forceinline__ void step_tile(const StepParams& a,
 template <int S, int V, bool GEN, bool CHECK>
 __global__ void __launch_bounds__(kThreads, CHECK ? 2 : (S == S_F32 ? LBM_MINB_F32 : (S == S_F16S ? LBM_MINB_F16S : LBM_MINB_F64)))
 k_step(const StepParams a, const Coef<typename StoreT<S>::T> c) {
-    using U = typename StoreT<S>::U;
     const int ntx = (a.nx + 32 * V - 1) / (32 * V);
     const int64_t ntiles = (int64_t)ntx * ((a.ny + BY - 1) / BY);
-    U acc[kRes] = {U(0), U(0), U(0), U(0), U(0)};
+    ResAcc<S> acc;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
         step_tile<S, V, GEN, CHECK>(a, c, tx, ty, acc);
     }
-    if (CHECK) residual_reduce<U>(a, acc);
+    if (CHECK) residual_reduce<S>(a, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -467,7 +564,7 @@ __device__ __forceinline__ int wrap_slot(int v, int n) {
 
 template <int S, bool GEN, bool CHECK, bool ANY>
 __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float>& c, float* sm,
-                                           int tx, int ty, float acc[kRes]) {
+                                           int tx, int ty, ResAcc<S>& acc) {
     constexpr int PL = kT2H * kT2W;             // shared-memory plane
     const int nx = a.nx, ny = a.ny;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -513,9 +610,8 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             }
         }
     }
-    float* __restrict__ snap = static_cast<float*>(a.snap);
     const int64_t n = (int64_t)nx * ny;
-    float so[kT2Rows][2][2];
+    ResSnap<S> so[kT2Rows][2];
     if (CHECK) {
 #pragma unroll
         for (int k = 0; k < kT2Rows; ++k) {
@@ -523,11 +619,8 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int col = lane + 32 * j, x = x0 + col;
-                so[k][j][0] = so[k][j][1] = 0.0f;
-                if (r >= 1 && r <= kT2H - 2 && y < ny && col >= 1 && col <= kT2W - 2 && x < nx) {
-                    so[k][j][0] = snap[(int64_t)y * nx + x];
-                    so[k][j][1] = snap[n + (int64_t)y * nx + x];
-                }
+                if (r >= 1 && r <= kT2H - 2 && y < ny && col >= 1 && col <= kT2W - 2 && x < nx)
+                    so[k][j] = snap_load<S>(a, n, (int64_t)y * nx + x);
             }
         }
     }
@@ -556,16 +649,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             f[7] = s[7 * PL + kT2W - 1];
             float u, v;
             scatter_local<S>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
-            if (CHECK) {
-                snap[idx] = u;
-                snap[n + idx] = v;
-                const float du = u - so[k][j][0], dv = v - so[k][j][1];
-                acc[0] = fmaxf(acc[0], fmaxf(fabsf(du), fabsf(dv)));
-                acc[1] = fmaxf(acc[1], fmaxf(fabsf(u), fabsf(v)));
-                acc[2] += du * du + dv * dv;
-                acc[3] += u * u + v * v;
-                if (!(isfinite(u) && isfinite(v))) acc[4] = 1.0f;
-            }
+            if (CHECK) check_node<S>(a, n, idx, acc, so[k][j], f, gx[k][j], gy[k][j], u, v);
         }
     }
 }
@@ -580,13 +664,13 @@ k_step2(const StepParams a, const Coef<float> c) {
     extern __shared__ float t2_smem[];
     const int ntx = (a.nx + kT2OX - 1) / kT2OX;
     const int64_t ntiles = (int64_t)ntx * ((a.ny + kT2OY - 1) / kT2OY);
-    float acc[kRes] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    ResAcc<S> acc;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
         step2_tile<S, GEN, CHECK, ANY>(a, c, t2_smem, tx, ty, acc);
         if (t + gridDim.x < ntiles) __syncthreads();   // slots are reused by the next tile
     }
-    if (CHECK) residual_reduce<float>(a, acc);
+    if (CHECK) residual_reduce<S>(a, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -621,7 +705,7 @@ constexpr int kT3Smem = 2 * 8 * kT3H * kT3W * (int)sizeof(float);
 
 template <int S, bool GEN, bool CHECK, bool ANY>
 __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float>& c, float* smA,
-                                           int tx, int ty, float acc[kRes]) {
+                                           int tx, int ty, ResAcc<S>& acc) {
     constexpr int PL = kT3H * kT3W;             // shared-memory plane
     float* smB = smA + 8 * PL;
     const int nx = a.nx, ny = a.ny;
@@ -688,9 +772,8 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
             for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
         }
     }
-    float* __restrict__ snap = static_cast<float*>(a.snap);
     const int64_t n = (int64_t)nx * ny;
-    float so[kT3Rows][2][2];
+    ResSnap<S> so[kT3Rows][2];
     if (CHECK) {
 #pragma unroll
         for (int k = 0; k < kT3Rows; ++k) {
@@ -698,11 +781,8 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int col = lane + 32 * j, x = x0 + col;
-                so[k][j][0] = so[k][j][1] = 0.0f;
-                if (r >= 2 && r <= kT3H - 3 && y < ny && col >= 2 && col <= kT3W - 3 && x < nx) {
-                    so[k][j][0] = snap[(int64_t)y * nx + x];
-                    so[k][j][1] = snap[n + (int64_t)y * nx + x];
-                }
+                if (r >= 2 && r <= kT3H - 3 && y < ny && col >= 2 && col <= kT3W - 3 && x < nx)
+                    so[k][j] = snap_load<S>(a, n, (int64_t)y * nx + x);
             }
         }
     }
@@ -731,16 +811,7 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
             f[7] = s[7 * PL + kT3W - 1];
             float u, v;
             scatter_local<S>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
-            if (CHECK) {
-                snap[idx] = u;
-                snap[n + idx] = v;
-                const float du = u - so[k][j][0], dv = v - so[k][j][1];
-                acc[0] = fmaxf(acc[0], fmaxf(fabsf(du), fabsf(dv)));
-                acc[1] = fmaxf(acc[1], fmaxf(fabsf(u), fabsf(v)));
-                acc[2] += du * du + dv * dv;
-                acc[3] += u * u + v * v;
-                if (!(isfinite(u) && isfinite(v))) acc[4] = 1.0f;
-            }
+            if (CHECK) check_node<S>(a, n, idx, acc, so[k][j], f, gx[k][j], gy[k][j], u, v);
         }
     }
 }
@@ -751,13 +822,13 @@ k_step3(const StepParams a, const Coef<float> c) {
     extern __shared__ float t3_smem[];
     const int ntx = (a.nx + kT3OX - 1) / kT3OX;
     const int64_t ntiles = (int64_t)ntx * ((a.ny + kT3OY - 1) / kT3OY);
-    float acc[kRes] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    ResAcc<S> acc;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int ty = (int)(t / ntx), tx = (int)(t - (int64_t)ty * ntx);
         step3_tile<S, GEN, CHECK, ANY>(a, c, t3_smem, tx, ty, acc);
         if (t + gridDim.x < ntiles) __syncthreads();   // slots are reused by the next tile
     }
-    if (CHECK) residual_reduce<float>(a, acc);
+    if (CHECK) residual_reduce<S>(a, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -767,24 +838,37 @@ k_step3(const StepParams a, const Coef<float> c) {
 // A block of 32*NW threads owns a strip of W = 32*NW slot columns (thread t
 // = column t for the whole launch) and a segment of `seg` output rows, and
 // walks down the segment one row per iteration at every step level at once:
-// in iteration i, step tau (1..T) updates row ybeg + i - 2*(tau - 1), so step
-// tau trails step tau - 1 by two rows and only reads rows that step tau - 1
+// in iteration i, step tau (1..T) updates the row of local index i - 2(tau - 1)
+// (local row j is lattice row ybeg + j, ybeg = y0 - (T - 1)), so step tau
+// trails step tau - 1 by two rows and only reads rows that step tau - 1
 // finished in earlier iterations.  Step 1 pulls f*(t) from global memory,
 // steps 2..T-1 pull from and write to rings of kWvD = 4 rows per level in
-// shared memory (row y in ring slot y mod 4), and step T stores f*(t+T) of
-// the strip's W - 2(T-1) inner columns to global memory.  One block barrier
-// per iteration separates a ring slot's last read from its next write.  The
-// halo costs 2(T-1) of W columns and 2(T - tau) extra rows of level tau per
-// segment, against 64 x 16 slots per 60 x 12 outputs of the three-step tile,
-// and a level's ring holds four rows instead of a whole tile, so four steps
-// per launch fit.  Latency: the force of a thread's column for the last
-// 2(T-1)+1 rows stays in registers (step tau uses the row step 1 loaded
-// 2(tau-1) iterations earlier), and step 1 issues the loads of its next row
-// before the shared-memory work of the current iteration (LBM_WV_PREF), so
-// no level waits on a global load it has just issued.  The per-node
-// arithmetic is the single step's: FP32 results equal T single-step launches
-// bit for bit (FP16S keeps the intermediate states in FP32).  Plain steps
-// only; lattices from W x 8 nodes up.
+// shared memory (local row j in ring slot j mod 4), and step T stores
+// f*(t+T) of the strip's W - 2(T-1) inner columns to global memory.  One
+// block barrier per iteration separates a ring slot's last read from its next
+// write.  The halo costs 2(T-1) of W columns and 2(T - tau) extra rows of
+// level tau per segment, and a level's ring holds four rows instead of a
+// whole tile, so four steps per launch fit.
+//
+// Instruction economy (the kernel issues, it does not wait on HBM): the
+// iterations in which every level is active run in groups of four, so every
+// ring slot is a compile-time offset from one per-thread address and no
+// level tests whether it is active; only the first 3(T-1) and the last few
+// iterations of a segment take the general path.  Latency: the force of a
+// thread's column for the last 2(T-1)+1 rows stays in registers (step tau
+// uses the row step 1 loaded 2(tau-1) iterations earlier), and step 1 issues
+// the loads of its next row before the shared-memory work of the current
+// iteration, so no level waits on a global load it has just issued.  With
+// I = int (lattices below 2^31 nodes) global addresses are a 32-bit in-plane
+// offset on a per-plane base.
+//
+// CHECK: step T is the residual-check step (its input state is u^(t+T-1));
+// its snapshot loads run one iteration ahead, and the block's partials go to
+// StepParams::partials (k_residual_finish combines them).
+//
+// The per-node arithmetic is the single step's: FP32 results equal T
+// single-step launches bit for bit (FP16S keeps the intermediate states in
+// FP32).  Lattices from W x 8 nodes up.
 #ifndef LBM_WV_NW
 #define LBM_WV_NW 8
 #endif
@@ -792,10 +876,7 @@ constexpr int kWvNW = LBM_WV_NW;                 // warps per block
 constexpr int kWvW = 32 * kWvNW;                 // strip width (slot columns)
 constexpr int kWvD = 4;                          // ring rows per level
 constexpr int kWvSegDefault = 128;               // output rows per block segment (default)
-#ifndef LBM_WV_PREF
-#define LBM_WV_PREF 1
-#endif
-constexpr bool kWvPref = LBM_WV_PREF != 0;       // level-1 loads one iteration ahead
+static_assert(kWvW == kThreads, "residual_reduce sizes its scratch by kThreads");
 template <int T> __host__ __device__ constexpr int wv_ox() { return kWvW - 2 * (T - 1); }
 template <int T> __host__ __device__ constexpr int wv_smem() { return (T - 1) * 8 * kWvD * kWvW * (int)sizeof(float); }
 // resident blocks per SM the kernel is compiled for: 228 KB of shared memory
@@ -805,11 +886,11 @@ template <int T> constexpr int wv_minb() {
                                                              : (2048 / kWvW);
 }
 
-template <int S, bool GEN, int T>
+template <int S, bool GEN, int T, bool CHECK, typename I>
 __global__ void __launch_bounds__(kWvW, wv_minb<T>())
 k_wave(const StepParams a, const Coef<float> c, int seg) {
     static_assert(T >= 2 && T <= 4, "two to four steps per launch");
-    constexpr int W = kWvW, OX = wv_ox<T>(), PL = kWvD * kWvW;
+    constexpr int W = kWvW, OX = wv_ox<T>(), PL = kWvD * kWvW, RP = 8 * PL, D = kWvD - 1;
     extern __shared__ float wv_ring[];            // (T-1) rings of 8 planes x kWvD rows x W
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
@@ -823,34 +904,40 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
     const bool store_ok = t >= T - 1 && t <= W - T && xs < nx;
     const float* __restrict__ gxp = static_cast<const float*>(a.gx);
     const float* __restrict__ gyp = static_cast<const float*>(a.gy);
-    const int ybeg = y0 - (T - 1);                // first row of level 1
+    const int ybeg = y0 - (T - 1);                // lattice row of local row 0 (level 1)
     const int iters = rows + 3 * (T - 1);
     const int n1 = rows + 2 * (T - 1);            // rows of level 1
-    // Force of the thread's column in rows y1, y1 - 1, ..., y1 - 2(T - 1) (y1 the
-    // row of level 1 in this iteration): level tau uses entry 2(tau - 1), so no
-    // level waits on a force load.
+    const int64_t n = (int64_t)nx * ny;
+    float* const rt = wv_ring + t;                // this thread's column of every ring
+    // Force of the thread's column in local rows i, i - 1, ..., i - 2(T - 1)
+    // (i the iteration): level tau uses entry 2(tau - 1).
     constexpr int NH = 2 * (T - 1) + 1;
     float hx[NH], hy[NH];
 #pragma unroll
     for (int k = 0; k < NH; ++k) hx[k] = hy[k] = 0.0f;
-    // Level 1 reads global memory LBM_WV_PREF rows ahead (0 or 1): the loads of
-    // row ybeg + i + 1 are then in flight while iteration i works from shared memory.
+    // Level 1 reads global memory one row ahead: the loads of local row i + 1
+    // are in flight while iteration i works from shared memory.
     Pulled<S> q;
-    float qg[2] = {0.0f, 0.0f};
+    float qg[2];
     auto load1 = [&](int i) {
         const int y = wrap_slot<false>(ybeg + i, ny);
-        const int64_t r0 = (int64_t)y * nx;
-        pull_load<S>(a, r0, (int64_t)wrap_dec(y, ny) * nx, (int64_t)wrap_inc(y, ny) * nx, x, xm, xp, q);
+        const I r0 = (I)y * nx;
+        pull_load<S, I>(a, r0, (I)wrap_dec(y, ny) * nx, (I)wrap_inc(y, ny) * nx, x, xm, xp, q);
         qg[0] = ldg(gxp + r0 + x);
         qg[1] = ldg(gyp + r0 + x);
     };
-    if (kWvPref) load1(0);
-    for (int i = 0; i < iters; ++i) {
-        // Level 1: rows ybeg .. y0 + rows - 1 + (T - 1), pulled from global memory.
-        const bool l1 = i < n1;
-        const int y1 = ybeg + i;
-        float f1[8];
-        if (!kWvPref && l1) load1(i);
+    // Residual check on level T: its snapshot entry is loaded one iteration ahead.
+    ResAcc<S> acc;
+    ResSnap<S> so;
+    auto snap_next = [&](int i) {
+        so = snap_load<S>(a, n, (int64_t)((I)(ybeg + i - 2 * (T - 1)) * nx + xs));
+    };
+
+    // One iteration; FULL: every level active (ring slots fold to constants
+    // when i is a compile-time offset from a multiple of four).
+    auto iter = [&](int i, auto full_c) {
+        constexpr bool FULL = decltype(full_c)::value;
+        const bool l1 = FULL || i < n1;
 #pragma unroll
         for (int k = NH - 1; k > 0; --k) {
             hx[k] = hx[k - 1];
@@ -858,51 +945,76 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
         }
         hx[0] = qg[0];
         hy[0] = qg[1];
+        float f1[8];
         if (l1) {
             pull_decode<S>(a, q, f1, c.theta);
-            if (kWvPref && i + 1 < n1) load1(i + 1);
+            if (FULL || i + 1 < n1) load1(i + 1);
         }
-        // Levels 2..T: row ybeg + i - 2(tau - 1), pulled from ring tau - 1.
+        // Levels T..2: local row j = i - 2(tau - 1), pulled from ring tau - 1.
 #pragma unroll
         for (int tau = T; tau >= 2; --tau) {
             // active rows y0 - (T - tau) .. y0 + rows - 1 + (T - tau)
-            if (i < 3 * (tau - 1) || i > rows + 2 * T + tau - 4) continue;
+            if (!FULL && (i < 3 * (tau - 1) || i > rows + 2 * T + tau - 4)) continue;
             if (tau < T ? (t < tau - 1 || t > W - tau) : !store_ok) continue;
-            const int yl = ybeg + i - 2 * (tau - 1);
-            const float* s = wv_ring + (tau - 2) * 8 * PL + t;
-            const int rm = ((yl - 1) & (kWvD - 1)) * W, r0 = (yl & (kWvD - 1)) * W,
-                      rp = ((yl + 1) & (kWvD - 1)) * W;
+            const int j = i - 2 * (tau - 1);
+            const float* sp = rt + (tau - 2) * RP;
+            const int rm = ((j - 1) & D) * W, r0 = (j & D) * W, rp = ((j + 1) & D) * W;
             float f[8];
-            f[0] = s[0 * PL + r0 - 1];          // f_p(x) = f*_p(x - c_p)
-            f[1] = s[1 * PL + rm];
-            f[2] = s[2 * PL + r0 + 1];
-            f[3] = s[3 * PL + rp];
-            f[4] = s[4 * PL + rm - 1];
-            f[5] = s[5 * PL + rm + 1];
-            f[6] = s[6 * PL + rp + 1];
-            f[7] = s[7 * PL + rp - 1];
+            f[0] = sp[0 * PL + r0 - 1];          // f_p(x) = f*_p(x - c_p)
+            f[1] = sp[1 * PL + rm];
+            f[2] = sp[2 * PL + r0 + 1];
+            f[3] = sp[3 * PL + rp];
+            f[4] = sp[4 * PL + rm - 1];
+            f[5] = sp[5 * PL + rm + 1];
+            f[6] = sp[6 * PL + rp + 1];
+            f[7] = sp[7 * PL + rp - 1];
             float u, v;
-            const Mom<float> m =
-                collide<float, GEN>(moments(f), hx[2 * (tau - 1)], hy[2 * (tau - 1)], c, u, v);
+            const float gx = hx[2 * (tau - 1)], gy = hy[2 * (tau - 1)];
+            const Mom<float> m = collide<float, GEN>(moments(f), gx, gy, c, u, v);
             if (tau < T) {
                 float fs[8];
                 populations(m, fs);
-                float* d = wv_ring + (tau - 1) * 8 * PL + r0 + t;
+                float* d = rt + (tau - 1) * RP + r0;
 #pragma unroll
                 for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
             } else {
-                scatter_local<S>(a, (int64_t)yl * nx + xs, m, c.qtheta);   // yl in [0, ny), xs < nx
+                const I idx = (I)(ybeg + j) * nx + xs;   // row in [y0, y0 + rows), xs < nx
+                if (CHECK) {
+                    check_node<S>(a, n, (int64_t)idx, acc, so, f, gx, gy, u, v);
+                    if (FULL || i + 1 < iters) snap_next(i + 1);
+                }
+                scatter_local<S>(a, (int64_t)idx, m, c.qtheta);
             }
         }
         if (l1) {
             float u, v, fs[8];
             populations(collide<float, GEN>(moments(f1), hx[0], hy[0], c, u, v), fs);
-            float* d = wv_ring + (y1 & (kWvD - 1)) * W + t;
+            float* d = rt + (i & D) * W;
 #pragma unroll
             for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
         }
         __syncthreads();
+    };
+
+    load1(0);
+    const int fb = 3 * (T - 1);                   // first iteration with every level active
+    const int fe = rows + 2 * T - 4;              // last one whose level 1 still prefetches
+    if (CHECK && store_ok) snap_next(fb);         // level T's first row is y0
+    const int m0 = (fb + 3) >> 2, m1 = (fe + 1) >> 2;   // groups i = 4m .. 4m + 3 within [fb, fe]
+    int i = 0;
+    if (m1 > m0) {
+        for (; i < 4 * m0; ++i) iter(i, std::false_type{});
+        for (int m = m0; m < m1; ++m) {
+            const int ib = m << 2;
+            iter(ib, std::true_type{});
+            iter(ib + 1, std::true_type{});
+            iter(ib + 2, std::true_type{});
+            iter(ib + 3, std::true_type{});
+        }
+        i = 4 * m1;
     }
+    for (; i < iters; ++i) iter(i, std::false_type{});
+    if (CHECK) residual_reduce<S>(a, acc);
 }
 
 // Solution fields of the current state (Table 2, Eq. compute_bared), FP64:
@@ -1091,10 +1203,12 @@ inline int64_t wave_blocks(int nx, int ny, int seg) {
     return (int64_t)((nx + wv_ox<T>() - 1) / wv_ox<T>()) * ((ny + seg - 1) / seg);
 }
 
-// T fused plain steps on the wavefront schedule (T = 3 or 4); defined with
-// each storage type's kernels.
-cudaError_t wave_f32(const StepParams& a, const Coef<float>& c, bool gen, int T, int seg, cudaStream_t st);
-cudaError_t wave_f16s(const StepParams& a, const Coef<float>& c, bool gen, int T, int seg, cudaStream_t st);
+// T fused steps on the wavefront schedule (T = 3 or 4; check: T = 4 with the
+// residual on the last step); defined with each storage type's kernels.
+cudaError_t wave_f32(const StepParams& a, const Coef<float>& c, bool gen, int T, bool check, int seg,
+                     cudaStream_t st);
+cudaError_t wave_f16s(const StepParams& a, const Coef<float>& c, bool gen, int T, bool check, int seg,
+                      cudaStream_t st);
 
 // Three fused steps (k_step3); defined with each storage type's kernels.
 cudaError_t step3_f32(const StepParams& a, const Coef<float>& c, bool gen, bool check,

@@ -47,15 +47,21 @@ int scratch_for_device(int dev, double** out) {
         int sms = 1;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
             sms = 1;
-        int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S_F64, 1, false, true>, kThreads, 0);
-        g_resident[dev][0][0] = sms * (b > 0 ? b : 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S_F64, 2, false, true>, kThreads, 0);
-        g_resident[dev][0][1] = sms * (b > 0 ? b : 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S_F32, 1, false, true>, kThreads, 0);
-        g_resident[dev][1][0] = sms * (b > 0 ? b : 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<S_F32, 4, false, true>, kThreads, 0);
-        g_resident[dev][1][1] = sms * (b > 0 ? b : 1);
+        // resident blocks of each check kernel, each query on its own (one
+        // block per SM where a query fails; its error is cleared so that the
+        // launch check below does not report it)
+        auto resident = [&](auto kernel) {
+            int b = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, 0) != cudaSuccess) {
+                cudaGetLastError();
+                b = 0;
+            }
+            return sms * (b > 0 ? b : 1);
+        };
+        g_resident[dev][0][0] = resident(k_step<S_F64, 1, false, true>);
+        g_resident[dev][0][1] = resident(k_step<S_F64, 2, false, true>);
+        g_resident[dev][1][0] = resident(k_step<S_F32, 1, false, true>);
+        g_resident[dev][1][1] = resident(k_step<S_F32, 4, false, true>);
     }
     *out = g_scratch_ptr[dev];
     return LBM_OK;

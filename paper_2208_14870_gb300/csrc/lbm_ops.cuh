@@ -75,45 +75,58 @@ static cudaError_t launch_step3(const StepParams& a, const Coef<float>& c, bool 
     return cudaGetLastError();
 }
 
-template <int S>
-static cudaError_t wv_allow_smem() {
+// One wavefront kernel: its dynamic shared memory (above 48 KB) is allowed
+// once per device, then it is launched.
+template <int S, bool GEN, int T, bool CHECK, typename I>
+static cudaError_t launch_wave_k(const StepParams& a, const Coef<float>& c, int seg, unsigned int grid,
+                                 cudaStream_t st) {
     static std::mutex mu;
     static bool done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (done[dev]) return cudaSuccess;
-    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    e = cudaFuncSetAttribute(k_wave<S, false, 3>, at, wv_smem<3>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wave<S, true, 3>, at, wv_smem<3>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wave<S, false, 4>, at, wv_smem<4>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wave<S, true, 4>, at, wv_smem<4>());
-    if (e == cudaSuccess) done[dev] = true;
-    return e;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done[dev]) {
+            e = cudaFuncSetAttribute(k_wave<S, GEN, T, CHECK, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     wv_smem<T>());
+            if (e != cudaSuccess) return e;
+            done[dev] = true;
+        }
+    }
+    k_wave<S, GEN, T, CHECK, I><<<grid, kWvW, wv_smem<T>(), st>>>(a, c, seg);
+    return cudaGetLastError();
 }
 
-// T = 3 or 4 fused plain steps on the wavefront schedule: one block per strip
-// and segment of seg output rows (the caller checks wave_fits).
+template <int S, bool GEN, int T, bool CHECK>
+static cudaError_t launch_wave_i(const StepParams& a, const Coef<float>& c, int seg, unsigned int grid,
+                                 cudaStream_t st) {
+    // 32-bit in-plane offsets while a plane has fewer than 2^31 nodes
+    if ((int64_t)a.nx * a.ny < (int64_t(1) << 31)) return launch_wave_k<S, GEN, T, CHECK, int>(a, c, seg, grid, st);
+    return launch_wave_k<S, GEN, T, CHECK, int64_t>(a, c, seg, grid, st);
+}
+
+// T = 3 or 4 fused steps on the wavefront schedule: one block per strip and
+// segment of seg output rows (the caller checks wave_fits).  check (T = 4
+// only): the last step is the residual-check step, one FP64 partial set per
+// block in StepParams::partials (wave_blocks<4> of them).
 template <int S>
-static cudaError_t launch_wave(const StepParams& a, const Coef<float>& c, bool gen, int T, int seg,
-                               cudaStream_t st) {
-    if ((T != 3 && T != 4) || seg < 1 || !wave_fits(a.nx, a.ny)) return cudaErrorInvalidValue;
-    cudaError_t e = wv_allow_smem<S>();
-    if (e != cudaSuccess) return e;
+static cudaError_t launch_wave(const StepParams& a, const Coef<float>& c, bool gen, int T, bool check,
+                               int seg, cudaStream_t st) {
+    if ((T != 3 && T != 4) || seg < 1 || !wave_fits(a.nx, a.ny) || (check && T != 4))
+        return cudaErrorInvalidValue;
     const int64_t blocks = T == 3 ? wave_blocks<3>(a.nx, a.ny, seg) : wave_blocks<4>(a.nx, a.ny, seg);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned int grid = (unsigned int)blocks;
-    const dim3 block(kWvW);
-    if (T == 3) {
-        if (gen) k_wave<S, true, 3><<<grid, block, wv_smem<3>(), st>>>(a, c, seg);
-        else k_wave<S, false, 3><<<grid, block, wv_smem<3>(), st>>>(a, c, seg);
-    } else {
-        if (gen) k_wave<S, true, 4><<<grid, block, wv_smem<4>(), st>>>(a, c, seg);
-        else k_wave<S, false, 4><<<grid, block, wv_smem<4>(), st>>>(a, c, seg);
-    }
-    return cudaGetLastError();
+    if (check)
+        return gen ? launch_wave_i<S, true, 4, true>(a, c, seg, grid, st)
+                   : launch_wave_i<S, false, 4, true>(a, c, seg, grid, st);
+    if (T == 3)
+        return gen ? launch_wave_i<S, true, 3, false>(a, c, seg, grid, st)
+                   : launch_wave_i<S, false, 3, false>(a, c, seg, grid, st);
+    return gen ? launch_wave_i<S, true, 4, false>(a, c, seg, grid, st)
+               : launch_wave_i<S, false, 4, false>(a, c, seg, grid, st);
 }
 
 // Two fused steps: one block per tile (check: up to check_blocks blocks).

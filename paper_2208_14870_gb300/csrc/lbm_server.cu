@@ -247,7 +247,7 @@ int lbm_server_create(size_t hbm_budget_bytes, int check_every, lbm_server** out
     // Each arena gets half of the budget; capacity in nodes from its bytes per
     // node (2 x populations + carriers + force and snapshot).
     const int64_t half = (int64_t)(hbm_budget_bytes / 2);
-    const int64_t per_node[2] = {2 * 32 + 16, 2 * (16 + 8) + 16};
+    const int64_t per_node[2] = {2 * 32 + 24, 2 * (16 + 8) + 24};
     const int max_probs = 4096;
     for (int a = 0; a < 2; ++a) {
         s->arena[a] = std::make_unique<ArenaEngine>();

@@ -4,7 +4,8 @@
 #include "lbm_ops.cuh"
 
 namespace lbm {
-cudaError_t wave_f16s(const StepParams& a, const Coef<float>& c, bool gen, int T, int seg, cudaStream_t st) {
-    return launch_wave<S_F16S>(a, c, gen, T, seg, st);
+cudaError_t wave_f16s(const StepParams& a, const Coef<float>& c, bool gen, int T, bool check, int seg,
+                      cudaStream_t st) {
+    return launch_wave<S_F16S>(a, c, gen, T, check, seg, st);
 }
 }  // namespace lbm

@@ -23,7 +23,9 @@ def simulate_launches(iters, check_every, spl, wave=False):
     by launch as the library plans it: plain steps grouped into launches of spl
     steps (four only on the wavefront schedule, else three), leftovers in
     shorter launches, and a check step (index + 1 a multiple of check_every)
-    as the last step of a launch of at most two steps."""
+    as the last step of a four-step wavefront launch (where the schedule runs
+    four steps per launch and the window has at least four steps), else of a
+    launch of at most two steps."""
     big = 4 if spl >= 4 and wave else min(spl, 3)
 
     def plain(m):
@@ -43,7 +45,8 @@ def simulate_launches(iters, check_every, spl, wave=False):
         if to_check > left:
             launches += plain(left)
             break
-        last = min(spl, 2, to_check)      # the check rides on a launch of at most two steps
+        # the check rides on a four-step wavefront launch or a launch of at most two steps
+        last = 4 if (spl >= 4 and wave and to_check >= 4) else min(spl, 2, to_check)
         launches += plain(to_check - last) + 1
         step += to_check
         left -= to_check
@@ -59,7 +62,7 @@ def test_launch_count_matches_the_schedule(bench, spl, wave):
     assert bench.launches_per_iterate(1000, 100, 2) == 500
     assert bench.launches_per_iterate(1000, 100, 1) == 1000
     assert bench.launches_per_iterate(1000, 100, 3) == 10 * (33 + 1)   # 98 = 32 x 3 + 2, then the check pair
-    assert bench.launches_per_iterate(1000, 100, 4, True) == 10 * (25 + 1)   # 98 = 24 x 4 + 2
+    assert bench.launches_per_iterate(1000, 100, 4, True) == 10 * 25   # 96 = 24 x 4, then the checked four
 
 
 def test_dominant_block(bench):
@@ -70,14 +73,16 @@ def test_dominant_block(bench):
     assert bench.dominant_block(100, 4) == (96, 3)          # four steps need the wavefront schedule
     assert bench.dominant_block(100, 4, True) == (96, 4)
     assert bench.dominant_block(21, 3) == (15, 3)          # 19 = 5 x 3 + 2 + 2
-    assert bench.dominant_block(11, 4, True) == (4, 4)      # 9 = 4 + 3 + 2
+    assert bench.dominant_block(11, 4, True) == (4, 4)      # 7 = 4 + 3, then the checked four
+    assert bench.dominant_block(13, 4, True) == (4, 4)      # 9 = 4 + 3 + 2
     for ce in range(1, 40):
         for spl, wave in ((1, False), (2, False), (3, False), (4, True)):
             block, big = bench.dominant_block(ce, spl, wave)
-            rest = bench.plan_plain(ce - min(spl, 2, ce) - block, spl, wave)
+            last = bench.check_launch_steps(ce, spl, wave)
+            rest = bench.plan_plain(ce - last - block, spl, wave)
             assert bench.plan_plain(block, spl, wave) == [big] * (block // big)
             assert sorted(bench.plan_plain(block, spl, wave) + rest, reverse=True) == \
-                sorted(bench.plan_plain(ce - min(spl, 2, ce), spl, wave), reverse=True)
+                sorted(bench.plan_plain(ce - last, spl, wave), reverse=True)
 
 
 def test_kernel_hash_ignores_comments_but_not_code(bench, tmp_path):

@@ -275,19 +275,23 @@ def test_f16s_force_rescale_keeps_state():
 @pytest.mark.parametrize("dtype", ["f32", "f16s"])
 def test_full_size_sampled_parity(dtype):
     """16384 x 16384 (the throughput workload) in the benchmark's launch
-    configuration (three steps per launch, plain and checked): after 6 steps
-    from the zero state every node depends on the force within 6 nodes, so sampled nodes are checked one by one against
-    the oracle run on a small periodic window around each sample."""
+    configuration: one plain four-step wavefront launch (k_wave, 128-row
+    segments) and one four-step wavefront launch whose last level carries the
+    residual check, as every residual window of the benchmark ends.  After 8
+    steps from the zero state every node depends on the force within 8 nodes,
+    so sampled nodes are checked one by one against the oracle run on a
+    small periodic window (19 x 19) around each sample."""
     n = 16384
-    steps = 6
+    steps = 8
     lam, mu = W.lame_2d(1.0, 0.3)
     rates = oracle.relaxation_rates(lam, mu)
     pw = W.random_force(n, n, 16, 8, seed=0x16384)
     gx, gy = W.random_force_grid(pw)
     with Lattice(n, n, lam, mu, dtype) as lat:
+        assert lat.steps_per_launch == 4 and lat.wavefront == -1
         lat.set_force(gx, gy)
-        lat.iterate(3)                  # one plain three-step launch
-        lat.iterate_checked(3, 3)       # and one three-step check launch
+        lat.iterate(4)                  # one plain four-step wavefront launch
+        lat.iterate_checked(4, 4)       # and one checked four-step wavefront launch
         out = torch.empty(5 * n * n, dtype=torch.float64, device="cuda")
         lat.fields_device(out)
         got = out.view(5, n, n)

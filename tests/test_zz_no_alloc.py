@@ -6,7 +6,12 @@ for cudaMalloc / cudaFree).  It runs the same kernel as the context API's
 lbm_iterate_checked with its reduction scratch in a static device array, so
 two calls in a row must reproduce, through the C ABI, what two residual-checked
 steps of a context give: the same populations and the same residual numbers
-within the FP64 tolerance of the parity tests (1e-12 relative).
+within the FP64 tolerance of the parity tests (1e-12 relative) -- with the
+default grid, with 3 blocks (many tiles per block, a three-slot last-block
+reduction) and with the largest grid the static scratch allows.
+
+The snapshot is 16 bytes per node for both storage types (two planes of
+doubles, or of (hi, lo) float pairs).
 
 This file is collected last on purpose.
 """
@@ -40,8 +45,11 @@ def rel(a, b):
     return float(np.max(np.abs(a - b))) / max(float(np.max(np.abs(b))), 1e-300)
 
 
-@pytest.mark.parametrize("dtype,nx,ny", [("f32", 300, 200), ("f64", 97, 61)])
-def test_noalloc_step_matches_context_api_twice(dtype, nx, ny):
+@pytest.mark.parametrize("grid", [0, 3, P.LBM_NOALLOC_MAX_BLOCKS])
+# (1024 x 1040 FP32 has 1040 tiles of 128 x 8 nodes: the largest grid is
+# 1024 blocks, some of which take two tiles)
+@pytest.mark.parametrize("dtype,nx,ny", [("f32", 300, 200), ("f64", 97, 61), ("f32", 1024, 1040)])
+def test_noalloc_step_matches_context_api_twice(dtype, nx, ny, grid):
     lam, mu = W.lame_2d(1.0, 0.3)
     pw = W.random_force(nx, ny, 6, 4, seed=77)
     gx, gy = W.random_force_grid(pw)
@@ -62,7 +70,7 @@ def test_noalloc_step_matches_context_api_twice(dtype, nx, ny):
     f_b = torch.zeros(8 * n, dtype=tdt, device="cuda")
     gxd = torch.from_numpy(gx).to(device="cuda", dtype=tdt).contiguous()
     gyd = torch.from_numpy(gy).to(device="cuda", dtype=tdt).contiguous()
-    snap = torch.zeros(2 * n, dtype=tdt, device="cuda")
+    snap = torch.zeros(2 * n, dtype=torch.float64, device="cuda")   # 16 bytes per node
     result = torch.zeros(5, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     bufs = [(f_a, f_b), (f_b, f_a)]
@@ -70,7 +78,7 @@ def test_noalloc_step_matches_context_api_twice(dtype, nx, ny):
         src, dst = bufs[k]
         P.lbm_step_checked_noalloc(nx, ny, lam, mu, code, src.data_ptr(), dst.data_ptr(),
                                    gxd.data_ptr(), gyd.data_ptr(), snap.data_ptr(),
-                                   result.data_ptr(), 0, stream)
+                                   result.data_ptr(), grid, stream)
         torch.cuda.synchronize()
         raw = result.cpu().numpy()
         fstar = dst.double().cpu().numpy().reshape(8, ny, nx)
@@ -93,7 +101,7 @@ def test_noalloc_rejects_more_blocks_than_its_scratch_holds():
     f_a = torch.zeros(8 * nx * ny, device="cuda")
     f_b = torch.zeros(8 * nx * ny, device="cuda")
     g = torch.zeros(nx * ny, device="cuda")
-    snap = torch.zeros(2 * nx * ny, device="cuda")
+    snap = torch.zeros(2 * nx * ny, dtype=torch.float64, device="cuda")   # 16 bytes per node
     result = torch.zeros(5, dtype=torch.float64, device="cuda")
     args = [nx, ny, lam, mu, P.LBM_F32, f_a.data_ptr(), f_b.data_ptr(), g.data_ptr(),
             g.data_ptr(), snap.data_ptr(), result.data_ptr()]
