@@ -464,6 +464,15 @@ int lbm_step_checked_noalloc(int nx, int ny, double lambda, double mu, int dtype
                              const void *f_src, void *f_dst, const void *gx, const void *gy,
                              void *snapshot, double *result, int grid_blocks, void *stream);
 
+/* Measured FP64 FMA throughput of the current device, in G thread-level FP64
+ * instructions per second (every SM full of threads running independent
+ * dependent-FMA chains, CUDA-event timed, about a quarter of a second).  The
+ * FP64 storage path is bound by the FP64 pipe, and this is its roofline
+ * denominator.  No counterpart in the paper.  Allocates and frees a small
+ * device buffer; synchronous.  LBM_ERR_ARG for a null pointer, LBM_ERR_CUDA
+ * if a CUDA call fails. */
+int lbm_fp64_fma_rate(double *ginst_per_s);
+
 /* Library version string. */
 const char *lbm_version(void);
 

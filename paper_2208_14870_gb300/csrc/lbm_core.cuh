@@ -123,9 +123,25 @@ __device__ __forceinline__ Mom<T> quarter(Mom<T> m) {
 //   f1 = P + A/2, f3 = P - A/2, f2 = Q + B/2, f4 = Q - B/2
 //   f5 = m22 + m11 + m12 + m21, f6 = m22 - m11 - m12 + m21,
 //   f7 = m22 + m11 - m12 - m21, f8 = m22 - m11 + m12 - m21.
-template <typename T>
+// ZERO22: the standard rates (w_22 = 1, so m*_22 = m^eq_22 = 0) drop m22
+// from the sums; that changes at most the sign of a zero population, so every
+// kernel running the standard rates uses this form.
+template <bool ZERO22 = false, typename T>
 __device__ __forceinline__ void populations(const Mom<T>& s, T f[8]) {
     const T A = fmad(T(-4), s.m12, s.m10), B = fmad(T(-4), s.m21, s.m01);
+    if (ZERO22) {
+        const T P = s.ms + s.md, Q = s.ms - s.md;
+        f[0] = fmad(T(0.5), A, P);
+        f[2] = fmad(T(-0.5), A, P);
+        f[1] = fmad(T(0.5), B, Q);
+        f[3] = fmad(T(-0.5), B, Q);
+        const T h3 = s.m12 + s.m21, h4 = s.m21 - s.m12;
+        f[4] = s.m11 + h3;
+        f[6] = s.m11 - h3;
+        f[5] = h4 - s.m11;
+        f[7] = -s.m11 - h4;
+        return;
+    }
     const T t = fmad(T(-2), s.m22, s.ms);
     const T P = t + s.md, Q = t - s.md;
     f[0] = fmad(T(0.5), A, P);

@@ -317,8 +317,8 @@ __device__ __forceinline__ void store_f16s(const StepParams& a, int64_t idx, con
 }
 
 // Store the post-collision state of node idx.
-// (s in the quarter form of collide; qtheta = theta / 4.)
-template <int S>
+// (s in the quarter form of collide; qtheta = theta / 4; GEN as for collide.)
+template <int S, bool GEN>
 __device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
                                               const Mom<typename StoreT<S>::T>& s,
                                               typename StoreT<S>::T qtheta) {
@@ -328,11 +328,11 @@ __device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
     const int64_t pl = a.plane;
     T f[8];
     if constexpr (S == S_F16S) {
-        populations(deviation_moments(s, qtheta), f);
+        populations<!GEN>(deviation_moments(s, qtheta), f);
         store_f16s(a, idx, f, s.m10, s.m01);
     } else {
         (void)qtheta;
-        populations(s, f);
+        populations<!GEN>(s, f);
 #pragma unroll
         for (int p = 0; p < 8; ++p) d[p * pl + idx] = P(f[p]);
     }
@@ -479,7 +479,7 @@ __device__ __forceinline__ void step_tile(const StepParams& a,
             const int64_t idx = r0 + x;
             T u, v;
             const Mom<T> s = collide<T, GEN>(moments(f[j]), gx[j], gy[j], c, u, v);
-            scatter_local<S>(a, idx, s, c.qtheta);
+            scatter_local<S, GEN>(a, idx, s, c.qtheta);
             if (CHECK) check_node<S>(a, n, idx, acc, so[j], f[j], gx[j], gy[j], u, v);
         }
     }
@@ -604,7 +604,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 float u, v, fs[8];
-                populations(collide<float, GEN>(moments(f[b][j]), gx[k][j], gy[k][j], c, u, v), fs);
+                populations<!GEN>(collide<float, GEN>(moments(f[b][j]), gx[k][j], gy[k][j], c, u, v), fs);
 #pragma unroll
                 for (int p = 0; p < 8; ++p) s[p * PL + 32 * j] = fs[p];
             }
@@ -648,7 +648,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             f[6] = s[6 * PL + kT2W + 1];
             f[7] = s[7 * PL + kT2W - 1];
             float u, v;
-            scatter_local<S>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
+            scatter_local<S, GEN>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
             if (CHECK) check_node<S>(a, n, idx, acc, so[k][j], f, gx[k][j], gy[k][j], u, v);
         }
     }
@@ -740,7 +740,7 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             float u, v, fs[8];
-            populations(collide<float, GEN>(moments(f[j]), gx[k][j], gy[k][j], c, u, v), fs);
+            populations<!GEN>(collide<float, GEN>(moments(f[j]), gx[k][j], gy[k][j], c, u, v), fs);
 #pragma unroll
             for (int p = 0; p < 8; ++p) s[p * PL + 32 * j] = fs[p];
         }
@@ -766,7 +766,7 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
             f[6] = s[6 * PL + kT3W + 1];
             f[7] = s[7 * PL + kT3W - 1];
             float u, v, fs[8];
-            populations(collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), fs);
+            populations<!GEN>(collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), fs);
             float* d = smB + r * kT3W + col;
 #pragma unroll
             for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
@@ -810,7 +810,7 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
             f[6] = s[6 * PL + kT3W + 1];
             f[7] = s[7 * PL + kT3W - 1];
             float u, v;
-            scatter_local<S>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
+            scatter_local<S, GEN>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
             if (CHECK) check_node<S>(a, n, idx, acc, so[k][j], f, gx[k][j], gy[k][j], u, v);
         }
     }
@@ -872,13 +872,18 @@ k_step3(const StepParams a, const Coef<float> c) {
 #ifndef LBM_WV_NW
 #define LBM_WV_NW 8
 #endif
+#ifndef LBM_WV_PREF2
+#define LBM_WV_PREF2 0
+#endif
 constexpr int kWvNW = LBM_WV_NW;                 // warps per block
 constexpr int kWvW = 32 * kWvNW;                 // strip width (slot columns)
+constexpr int kWvRow = kWvW + 2;                 // ring row: the strip plus one pad column per side
 constexpr int kWvD = 4;                          // ring rows per level
 constexpr int kWvSegDefault = 128;               // output rows per block segment (default)
-static_assert(kWvW == kThreads, "residual_reduce sizes its scratch by kThreads");
+constexpr bool kWvPref2 = LBM_WV_PREF2 != 0;     // level-1 loads two rows ahead (else one)
+static_assert(kWvW <= kThreads, "residual_reduce sizes its scratch by kThreads");
 template <int T> __host__ __device__ constexpr int wv_ox() { return kWvW - 2 * (T - 1); }
-template <int T> __host__ __device__ constexpr int wv_smem() { return (T - 1) * 8 * kWvD * kWvW * (int)sizeof(float); }
+template <int T> __host__ __device__ constexpr int wv_smem() { return (T - 1) * 8 * kWvD * kWvRow * (int)sizeof(float); }
 // resident blocks per SM the kernel is compiled for: 228 KB of shared memory
 // per SM, 1 KB reserved per block
 template <int T> constexpr int wv_minb() {
@@ -890,8 +895,8 @@ template <int S, bool GEN, int T, bool CHECK, typename I>
 __global__ void __launch_bounds__(kWvW, wv_minb<T>())
 k_wave(const StepParams a, const Coef<float> c, int seg) {
     static_assert(T >= 2 && T <= 4, "two to four steps per launch");
-    constexpr int W = kWvW, OX = wv_ox<T>(), PL = kWvD * kWvW, RP = 8 * PL, D = kWvD - 1;
-    extern __shared__ float wv_ring[];            // (T-1) rings of 8 planes x kWvD rows x W
+    constexpr int W = kWvW, R = kWvRow, OX = wv_ox<T>(), PL = kWvD * kWvRow, RP = 8 * PL, D = kWvD - 1;
+    extern __shared__ float wv_ring[];            // (T-1) rings of 8 planes x kWvD rows x kWvRow
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
     const int nstrips = (nx + OX - 1) / OX;
@@ -908,23 +913,31 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
     const int iters = rows + 3 * (T - 1);
     const int n1 = rows + 2 * (T - 1);            // rows of level 1
     const int64_t n = (int64_t)nx * ny;
-    float* const rt = wv_ring + t;                // this thread's column of every ring
+    // This thread's column of every ring (slot t sits at padded column t + 1,
+    // so the pulls of t - 1 and t + 1 stay inside the row for every thread).
+    float* const rt = wv_ring + t + 1;
     // Force of the thread's column in local rows i, i - 1, ..., i - 2(T - 1)
     // (i the iteration): level tau uses entry 2(tau - 1).
     constexpr int NH = 2 * (T - 1) + 1;
     float hx[NH], hy[NH];
 #pragma unroll
     for (int k = 0; k < NH; ++k) hx[k] = hy[k] = 0.0f;
-    // Level 1 reads global memory one row ahead: the loads of local row i + 1
-    // are in flight while iteration i works from shared memory.
-    Pulled<S> q;
-    float qg[2];
-    auto load1 = [&](int i) {
-        const int y = wrap_slot<false>(ybeg + i, ny);
-        const I r0 = (I)y * nx;
-        pull_load<S, I>(a, r0, (I)wrap_dec(y, ny) * nx, (I)wrap_inc(y, ny) * nx, x, xm, xp, q);
-        qg[0] = ldg(gxp + r0 + x);
-        qg[1] = ldg(gyp + r0 + x);
+    // Level 1 reads global memory one (LBM_WV_PREF2: two) rows ahead, so its
+    // loads are in flight while the iterations before work from shared
+    // memory.  The row offsets of the next row to load advance one row per
+    // load (rows are loaded in order), with the periodic wrap.
+    Pulled<S> q[kWvPref2 ? 2 : 1];
+    float qg[kWvPref2 ? 2 : 1][2];
+    int ly = wrap_slot<false>(ybeg, ny);          // lattice row of the next load
+    I lr0 = (I)ly * nx, lrm = (I)wrap_dec(ly, ny) * nx, lrp = (I)wrap_inc(ly, ny) * nx;
+    auto load1 = [&](int b) {
+        pull_load<S, I>(a, lr0, lrm, lrp, x, xm, xp, q[b]);
+        qg[b][0] = ldg(gxp + lr0 + x);
+        qg[b][1] = ldg(gyp + lr0 + x);
+        ly = wrap_inc(ly, ny);
+        lrm = lr0;
+        lr0 = lrp;
+        lrp = (I)wrap_inc(ly, ny) * nx;
     };
     // Residual check on level T: its snapshot entry is loaded one iteration ahead.
     ResAcc<S> acc;
@@ -934,31 +947,35 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
     };
 
     // One iteration; FULL: every level active (ring slots fold to constants
-    // when i is a compile-time offset from a multiple of four).
+    // when i is a compile-time offset from a multiple of four).  Halo threads
+    // of a level compute values no valid slot reads (their pulls stay inside
+    // the padded ring rows), so no level branches per thread; only the
+    // stores of level T are predicated.
     auto iter = [&](int i, auto full_c) {
         constexpr bool FULL = decltype(full_c)::value;
         const bool l1 = FULL || i < n1;
+        const int b = kWvPref2 ? (i & 1) : 0;     // load buffer of local row i
 #pragma unroll
         for (int k = NH - 1; k > 0; --k) {
             hx[k] = hx[k - 1];
             hy[k] = hy[k - 1];
         }
-        hx[0] = qg[0];
-        hy[0] = qg[1];
+        hx[0] = qg[b][0];
+        hy[0] = qg[b][1];
         float f1[8];
         if (l1) {
-            pull_decode<S>(a, q, f1, c.theta);
-            if (FULL || i + 1 < n1) load1(i + 1);
+            pull_decode<S>(a, q[b], f1, c.theta);
+            const int next = kWvPref2 ? i + 2 : i + 1;
+            if (FULL || next < n1) load1(b);
         }
         // Levels T..2: local row j = i - 2(tau - 1), pulled from ring tau - 1.
 #pragma unroll
         for (int tau = T; tau >= 2; --tau) {
             // active rows y0 - (T - tau) .. y0 + rows - 1 + (T - tau)
             if (!FULL && (i < 3 * (tau - 1) || i > rows + 2 * T + tau - 4)) continue;
-            if (tau < T ? (t < tau - 1 || t > W - tau) : !store_ok) continue;
             const int j = i - 2 * (tau - 1);
             const float* sp = rt + (tau - 2) * RP;
-            const int rm = ((j - 1) & D) * W, r0 = (j & D) * W, rp = ((j + 1) & D) * W;
+            const int rm = ((j - 1) & D) * R, r0 = (j & D) * R, rp = ((j + 1) & D) * R;
             float f[8];
             f[0] = sp[0 * PL + r0 - 1];          // f_p(x) = f*_p(x - c_p)
             f[1] = sp[1 * PL + rm];
@@ -973,23 +990,23 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
             const Mom<float> m = collide<float, GEN>(moments(f), gx, gy, c, u, v);
             if (tau < T) {
                 float fs[8];
-                populations(m, fs);
+                populations<!GEN>(m, fs);
                 float* d = rt + (tau - 1) * RP + r0;
 #pragma unroll
                 for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
-            } else {
+            } else if (store_ok) {
                 const I idx = (I)(ybeg + j) * nx + xs;   // row in [y0, y0 + rows), xs < nx
                 if (CHECK) {
                     check_node<S>(a, n, (int64_t)idx, acc, so, f, gx, gy, u, v);
                     if (FULL || i + 1 < iters) snap_next(i + 1);
                 }
-                scatter_local<S>(a, (int64_t)idx, m, c.qtheta);
+                scatter_local<S, GEN>(a, (int64_t)idx, m, c.qtheta);
             }
         }
         if (l1) {
             float u, v, fs[8];
-            populations(collide<float, GEN>(moments(f1), hx[0], hy[0], c, u, v), fs);
-            float* d = rt + (i & D) * W;
+            populations<!GEN>(collide<float, GEN>(moments(f1), hx[0], hy[0], c, u, v), fs);
+            float* d = rt + (i & D) * R;
 #pragma unroll
             for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
         }
@@ -997,8 +1014,10 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
     };
 
     load1(0);
+    if (kWvPref2 && n1 > 1) load1(1);
     const int fb = 3 * (T - 1);                   // first iteration with every level active
-    const int fe = rows + 2 * T - 4;              // last one whose level 1 still prefetches
+    // last one whose level 1 still loads ahead
+    const int fe = rows + 2 * T - 3 - (kWvPref2 ? 2 : 1);
     if (CHECK && store_ok) snap_next(fb);         // level T's first row is y0
     const int m0 = (fb + 3) >> 2, m1 = (fe + 1) >> 2;   // groups i = 4m .. 4m + 3 within [fb, fe]
     int i = 0;

@@ -86,6 +86,7 @@ _SIGS = {
     "lbm_get_rates": (_c.c_int, [_vp, _c.POINTER(lbm_rates)]),
     "lbm_get_device_bytes": (_c.c_int, [_vp, _c.POINTER(_c.c_size_t)]),
     "lbm_last_error": (_c.c_char_p, []),
+    "lbm_fp64_fma_rate": (_c.c_int, [_c.POINTER(_c.c_double)]),
     "lbm_step_checked_noalloc": (_c.c_int, [_c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_int,
                                             _vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp]),
     "lbm_version": (_c.c_char_p, []),
@@ -296,6 +297,14 @@ def lbm_step_checked_noalloc(nx: int, ny: int, lam: float, mu: float, dtype: int
                            "LBM_F32, 1 <= nx, ny, nx*ny <= 2^31, mu > 0, lambda + mu > 0, "
                            "non-null distinct buffers, 0 <= grid_blocks <= %d)"
                        % LBM_NOALLOC_MAX_BLOCKS)
+
+
+def lbm_fp64_fma_rate() -> float:
+    """Measured FP64 FMA throughput of the current device (G thread-level
+    FP64 instructions per second)."""
+    r = ctypes.c_double()
+    _check(_lib.lbm_fp64_fma_rate(ctypes.byref(r)), "lbm_fp64_fma_rate")
+    return r.value
 
 
 def lbm_version() -> str:
