@@ -879,7 +879,7 @@ constexpr int kWvNW = LBM_WV_NW;                 // warps per block
 constexpr int kWvW = 32 * kWvNW;                 // strip width (slot columns)
 constexpr int kWvRow = kWvW + 2;                 // ring row: the strip plus one pad column per side
 constexpr int kWvD = 4;                          // ring rows per level
-constexpr int kWvSegDefault = 128;               // output rows per block segment (default)
+constexpr int kWvSegDefault = 256;               // output rows per block segment (default)
 constexpr bool kWvPref2 = LBM_WV_PREF2 != 0;     // level-1 loads two rows ahead (else one)
 static_assert(kWvW <= kThreads, "residual_reduce sizes its scratch by kThreads");
 template <int T> __host__ __device__ constexpr int wv_ox() { return kWvW - 2 * (T - 1); }
