@@ -306,10 +306,19 @@ const char *lbm_last_error(void);
  * code 1, 2, 4: warps of 32 columns, one step per barrier) or, when
  * check_every is even, LBM_TILE_TWO_STEP tiles (62 x 22 nodes, two steps per
  * tile visit with the intermediate state on chip and one grid barrier per
- * pair of steps; lbm_set_steps_per_launch describes the arithmetic).
+ * pair of steps; lbm_set_steps_per_launch describes the arithmetic) or, when
+ * check_every is a multiple of 4, the wavefront chunk LBM_TILE_WAVE: problems
+ * at least 256 columns wide and 8 rows high advance four steps per visit of a
+ * wavefront item (a 256-column strip by 64 rows on the schedule of
+ * lbm_set_wavefront), narrower ones two steps per two-step tile, with two grid
+ * barriers per four steps and items taken from a work counter, wavefront
+ * items first.  Every tile code computes the same per-node arithmetic; FP32
+ * results are the same bits under every code.
  * ------------------------------------------------------------------------- */
-/* Tile code of two-step tiles in lbm_batch_report.tile_v and lbm_stats.tile_v. */
+/* Tile codes in lbm_batch_report.tile_v and lbm_stats.tile_v besides the
+ * widths 1, 2, 4: two-step tiles, and the wavefront chunk. */
 #define LBM_TILE_TWO_STEP 3
+#define LBM_TILE_WAVE 5
 
 typedef struct lbm_problem {
     int nx, ny;                 /* lattice size, >= 1 */
@@ -327,7 +336,7 @@ typedef struct lbm_result {
 } lbm_result;
 
 typedef struct lbm_batch_report {
-    int tile_v;                 /* tile code used: 1, 2, 4 (warps of 32 columns) or LBM_TILE_TWO_STEP */
+    int tile_v;                 /* tile code used: 1, 2, 4 (warps of 32 columns), LBM_TILE_TWO_STEP or LBM_TILE_WAVE */
     int blocks;                 /* grid of the persistent chunk kernel */
     int64_t chunks;             /* chunk launches */
     int64_t lattice_updates;    /* sum over problems of nodes x steps */
@@ -377,7 +386,7 @@ typedef struct lbm_stats {
     int64_t chunks;
     size_t hbm_bytes;          /* device memory held by the arenas */
     int peak_running;          /* most problems resident at once */
-    int tile_v;                /* tile code: 1, 2, 4 (warps of 32 columns) or LBM_TILE_TWO_STEP */
+    int tile_v;                /* tile code: 1, 2, 4 (warps of 32 columns), LBM_TILE_TWO_STEP or LBM_TILE_WAVE */
     int failed;                /* LBM_OK, or the error that stopped the worker */
 } lbm_stats;
 

@@ -41,6 +41,8 @@ struct BatchArgs {
     const BatchProb* probs;
     const uint2* tiles;        // (problem, tile)
     const int* ntiles;         // device scalar: number of valid tiles
+    const int* nwide;          // wavefront chunks: the first *nwide tiles are wavefront items
+    int* counters;             // wavefront chunks: one work counter per phase, zero at launch
     char* pop0;
     char* pop1;
     char* car0;
@@ -105,15 +107,30 @@ private:
 // per tile visit and one grid barrier per pair of steps (chunk length even).
 constexpr int kTileTwoStep = 3;
 
+// Tile code of the wavefront chunk: problems from one strip width up advance
+// four steps per visit of a wavefront item (one strip, kArenaWaveSeg rows);
+// narrower ones take two two-step tiles per four steps (chunk length a
+// multiple of 4).
+constexpr int kTileWave = 5;
+constexpr int kArenaWaveSeg = 64;
+
+// (wavefront items address a problem with 32-bit in-plane offsets)
+inline bool arena_wide(int nx, int ny) { return wave_fits(nx, ny) && (int64_t)nx * ny < (int64_t(1) << 31); }
+
 // Number of tiles of an nx x ny problem for tile code V.
 inline int64_t arena_tiles(int nx, int ny, int V) {
+    if (V == kTileWave)
+        return arena_wide(nx, ny) ? (int64_t)((nx + wv_ox<4>() - 1) / wv_ox<4>()) *
+                                        ((ny + kArenaWaveSeg - 1) / kArenaWaveSeg)
+                                  : step2_tiles(nx, ny);
     return V == kTileTwoStep ? step2_tiles(nx, ny) : step_tiles(nx, ny, V);
 }
 
 // Launch one chunk: nsteps steps of every listed tile (all of storage type
 // dtype: S_F32 or S_F16S), residual check fused into the last step.  Tile
-// code V: width 32*V for V in {1, 2, 4}, or kTileTwoStep.  Cooperative
-// launch: grid must not exceed arena_occupancy(dtype, V) x SM count.
+// code V: width 32*V for V in {1, 2, 4}, kTileTwoStep or kTileWave.
+// Cooperative launch: grid must not exceed arena_occupancy(dtype, V) x SM
+// count.
 cudaError_t launch_arena_chunk(int dtype, int V, const BatchArgs& a, int grid, cudaStream_t st);
 // Resident blocks per SM of the chunk kernel.
 int arena_occupancy(int dtype, int V);

@@ -88,15 +88,22 @@ extern "C" int lbm_batch_solve(int count, const lbm_problem* probs, int dtype, d
         // and, for an even chunk length, with two-step tiles; the fastest per
         // active node and chunk is kept and cached.
         const std::string key = signature(count, probs, dtype, check_every);
-        const bool even = check_every % 2 == 0;
+        const bool even = check_every % 2 == 0, four = check_every % 4 == 0;
         int V = rc == LBM_OK ? autotune_lookup(key) : 0;
-        if (V == kTileTwoStep && !even) V = 0;
+        if ((V == kTileTwoStep && !even) || (V == kTileWave && !four)) V = 0;
         if (const char* force_v = std::getenv("LBM_BATCH_TILE_V")) {  // fixed shape, no tuning
             const int fv = std::atoi(force_v);
-            if (fv == 1 || fv == 2 || fv == 4 || (fv == kTileTwoStep && even)) V = fv;
+            if (fv == 1 || fv == 2 || fv == 4 || (fv == kTileTwoStep && even) || (fv == kTileWave && four))
+                V = fv;
         }
-        const int cand[4] = {1, 2, 4, kTileTwoStep};
-        const int ncand = even ? 4 : 3;
+        // candidates, the likeliest first (the wavefront chunk when the chunk
+        // length allows it)
+        int cand[5], ncand = 0;
+        if (four) cand[ncand++] = kTileWave;
+        if (even) cand[ncand++] = kTileTwoStep;
+        cand[ncand++] = 4;
+        cand[ncand++] = 2;
+        cand[ncand++] = 1;
         double best = 1e300;
         int tuning = V == 0 ? 0 : ncand;
         while (rc == LBM_OK && eng.running() > 0) {

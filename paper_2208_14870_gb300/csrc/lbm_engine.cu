@@ -12,6 +12,7 @@
 #include "lbm_engine.cuh"
 
 static_assert(lbm::kTileTwoStep == LBM_TILE_TWO_STEP, "tile code of two-step tiles");
+static_assert(lbm::kTileWave == LBM_TILE_WAVE, "tile code of the wavefront chunk");
 
 namespace lbm {
 
@@ -48,6 +49,8 @@ ArenaEngine::~ArenaEngine() {
     if (d_acc_) cudaFree(d_acc_);
     if (d_tiles_) cudaFree(d_tiles_);
     if (d_ntiles_) cudaFree(d_ntiles_);
+    if (d_nwide_) cudaFree(d_nwide_);
+    if (d_counters_) cudaFree(d_counters_);
     if (d_fields_) cudaFree(d_fields_);
     if (h_acc_) cudaFreeHost(h_acc_);
     if (h_tiles_) cudaFreeHost(h_tiles_);
@@ -98,6 +101,9 @@ int ArenaEngine::init(int dtype, int64_t node_capacity, int max_probs, int check
     ECK(cudaMallocHost(&h_acc_, sizeof(double) * kRes * max_probs));
     ECK(cudaMalloc(&d_ntiles_, sizeof(int)));
     ECK(cudaMemsetAsync(d_ntiles_, 0, sizeof(int), st_));
+    ECK(cudaMalloc(&d_nwide_, sizeof(int)));
+    ECK(cudaMemsetAsync(d_nwide_, 0, sizeof(int), st_));
+    ECK(cudaMalloc(&d_counters_, sizeof(int) * 2 * (k_ / 4 + 1)));
     ECK(cudaEventCreate(&ev0_));
     ECK(cudaEventCreate(&ev1_));
     dev_bytes_ += sizeof(BatchProb) * max_probs + sizeof(double) * kRes * max_probs;
@@ -242,29 +248,38 @@ int ArenaEngine::upload_tiles(int V, std::string* err) {
             }
     }
     ECK(cudaStreamSynchronize(st_));  // the pinned list may feed a previous copy
-    int64_t t = 0;
-    for (int s = 0; s < (int)probs_.size(); ++s) {
-        const HostProb& p = probs_[s];
-        if (p.state != P_RUNNING) continue;
-        const int64_t m = arena_tiles(p.nx, p.ny, V);
-        for (int64_t i = 0; i < m; ++i) h_tiles_[t++] = make_uint2((unsigned)s, (unsigned)i);
+    // wavefront chunks list the wide problems' wavefront items first, then the
+    // narrow problems' two-step tiles
+    int64_t t = 0, nwide = 0;
+    for (int pass = (V == kTileWave ? 0 : 1); pass < 2; ++pass) {
+        for (int s = 0; s < (int)probs_.size(); ++s) {
+            const HostProb& p = probs_[s];
+            if (p.state != P_RUNNING) continue;
+            if (V == kTileWave && arena_wide(p.nx, p.ny) != (pass == 0)) continue;
+            const int64_t m = arena_tiles(p.nx, p.ny, V);
+            for (int64_t i = 0; i < m; ++i) h_tiles_[t++] = make_uint2((unsigned)s, (unsigned)i);
+        }
+        if (pass == 0) nwide = t;
     }
-    static thread_local int nt_host;
-    nt_host = (int)nt;
+    static thread_local int nt_host[2];
+    nt_host[0] = (int)nt;
+    nt_host[1] = (int)nwide;
     if (nt > 0) ECK(cudaMemcpyAsync(d_tiles_, h_tiles_, sizeof(uint2) * nt, cudaMemcpyHostToDevice, st_));
-    ECK(cudaMemcpyAsync(d_ntiles_, &nt_host, sizeof(int), cudaMemcpyHostToDevice, st_));
+    ECK(cudaMemcpyAsync(d_ntiles_, &nt_host[0], sizeof(int), cudaMemcpyHostToDevice, st_));
+    ECK(cudaMemcpyAsync(d_nwide_, &nt_host[1], sizeof(int), cudaMemcpyHostToDevice, st_));
     ECK(cudaStreamSynchronize(st_));
     tiles_V_ = V;
     tiles_dirty_ = false;
     return LBM_OK;
 }
 
-int ArenaEngine::ensure_graph(int V, std::string* err) {
-    if (graph_[V] || graph_failed_[V]) return LBM_OK;
+BatchArgs ArenaEngine::chunk_args() const {
     BatchArgs a{};
     a.probs = d_probs_;
     a.tiles = d_tiles_;
     a.ntiles = d_ntiles_;
+    a.nwide = d_nwide_;
+    a.counters = d_counters_;
     a.pop0 = pop_[0];
     a.pop1 = pop_[1];
     a.car0 = car_[0];
@@ -272,6 +287,12 @@ int ArenaEngine::ensure_graph(int V, std::string* err) {
     a.fs = fs_;
     a.acc = d_acc_;
     a.nsteps = k_;
+    return a;
+}
+
+int ArenaEngine::ensure_graph(int V, std::string* err) {
+    if (graph_[V] || graph_failed_[V]) return LBM_OK;
+    const BatchArgs a = chunk_args();
     const int grid = grid_blocks(V);
     if (grid < 1) {
         if (err) *err = "arena: chunk kernel cannot be resident";
@@ -281,6 +302,7 @@ int ArenaEngine::ensure_graph(int V, std::string* err) {
     cudaError_t e = cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(d_acc_, 0, sizeof(double) * kRes * probs_.size(), st_);
+        if (V == kTileWave) cudaMemsetAsync(d_counters_, 0, sizeof(int) * 2 * (k_ / 4), st_);
         launch_arena_chunk(dtype_, V, a, grid, st_);
         cudaMemcpyAsync(h_acc_, d_acc_, sizeof(double) * kRes * probs_.size(), cudaMemcpyDeviceToHost, st_);
         e = cudaStreamEndCapture(st_, &g);
@@ -296,8 +318,9 @@ int ArenaEngine::ensure_graph(int V, std::string* err) {
 }
 
 int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
-    if (V != 1 && V != 2 && V != 4 && !(V == kTileTwoStep && k_ % 2 == 0)) {
-        if (err) *err = "arena: tile code must be 1, 2 or 4 warps of 32, or two-step tiles with an even chunk";
+    if (V != 1 && V != 2 && V != 4 && !(V == kTileTwoStep && k_ % 2 == 0) && !(V == kTileWave && k_ % 4 == 0)) {
+        if (err) *err = "arena: tile code must be 1, 2 or 4 warps of 32, two-step tiles with an even chunk, "
+                        "or the wavefront chunk with a chunk of a multiple of 4 steps";
         return LBM_ERR_ARG;
     }
     if (device_ms) *device_ms = 0.0f;
@@ -345,18 +368,9 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
     if (graph_[V]) {
         ECK(cudaGraphLaunch(graph_[V], st_));
     } else {
-        BatchArgs a{};
-        a.probs = d_probs_;
-        a.tiles = d_tiles_;
-        a.ntiles = d_ntiles_;
-        a.pop0 = pop_[0];
-        a.pop1 = pop_[1];
-        a.car0 = car_[0];
-        a.car1 = car_[1];
-        a.fs = fs_;
-        a.acc = d_acc_;
-        a.nsteps = k_;
+        const BatchArgs a = chunk_args();
         ECK(cudaMemsetAsync(d_acc_, 0, sizeof(double) * kRes * probs_.size(), st_));
+        if (V == kTileWave) ECK(cudaMemsetAsync(d_counters_, 0, sizeof(int) * 2 * (k_ / 4), st_));
         ECK(launch_arena_chunk(dtype_, V, a, grid_blocks(V), st_));
         ECK(cudaMemcpyAsync(h_acc_, d_acc_, sizeof(double) * kRes * probs_.size(), cudaMemcpyDeviceToHost, st_));
     }
@@ -368,8 +382,11 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
         if (p.state != P_RUNNING) continue;
         p.steps += k_;
         p.lups += p.n * k_;
-        // the buffers swap once per launch-level step: k steps, or k/2 pairs
-        if ((V == kTileTwoStep ? (k_ / 2) : k_) & 1) {
+        // the buffers swap once per launch-level step: k steps, k/2 pairs, or
+        // (wavefront chunk) k/4 passes of a wide problem, k/2 pairs of a narrow one
+        const int64_t swaps = V == kTileWave ? (arena_wide(p.nx, p.ny) ? k_ / 4 : k_ / 2)
+                                             : (V == kTileTwoStep ? k_ / 2 : k_);
+        if (swaps & 1) {
             p.parity ^= 1;
             desc_dirty_ = true;
         }

@@ -74,6 +74,7 @@ public:
 
 private:
     int upload_tiles(int V, std::string* err);
+    BatchArgs chunk_args() const;
     cudaError_t launch_fields(int slot, double* dst);
     int ensure_fields_buffer(int64_t len, std::string* err);
     int ensure_graph(int V, std::string* err);
@@ -93,6 +94,8 @@ private:
     uint2* d_tiles_ = nullptr;
     int64_t tiles_cap_ = 0;
     int* d_ntiles_ = nullptr;
+    int* d_nwide_ = nullptr;          // wavefront chunks: wavefront items at the list's head
+    int* d_counters_ = nullptr;       // wavefront chunks: a work counter per phase (2 per pass)
     uint2* h_tiles_ = nullptr;        // pinned
     int64_t h_tiles_cap_ = 0;
     int tiles_V_ = 0;                 // V the device tile list was built for
@@ -103,8 +106,8 @@ private:
     double* d_fields_ = nullptr;      // FP64 staging for recovery
     int64_t d_fields_cap_ = 0;
     double* h_fields_ = nullptr;      // pinned block for recover_many
-    cudaGraphExec_t graph_[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    bool graph_failed_[5] = {false, false, false, false, false};
+    cudaGraphExec_t graph_[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool graph_failed_[6] = {false, false, false, false, false, false};
     cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
     int nrunning_ = 0;
     int64_t dev_bytes_ = 0;

@@ -891,18 +891,18 @@ template <int T> constexpr int wv_minb() {
                                                              : (2048 / kWvW);
 }
 
+// One block's share of a wavefront launch: strip `strip`, output rows y0 ..
+// y0 + rows - 1, T steps; wv_ring is the block's (T-1) rings.  With CHECK the
+// thread's residual partials of level T are accumulated into acc.  Called by
+// k_wave (one block per strip and segment) and by the batched arena (one
+// call per work item).
 template <int S, bool GEN, int T, bool CHECK, typename I>
-__global__ void __launch_bounds__(kWvW, wv_minb<T>())
-k_wave(const StepParams a, const Coef<float> c, int seg) {
+__device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float>& c, float* wv_ring,
+                                           int strip, int y0, int rows, ResAcc<S>& acc) {
     static_assert(T >= 2 && T <= 4, "two to four steps per launch");
     constexpr int W = kWvW, R = kWvRow, OX = wv_ox<T>(), PL = kWvD * kWvRow, RP = 8 * PL, D = kWvD - 1;
-    extern __shared__ float wv_ring[];            // (T-1) rings of 8 planes x kWvD rows x kWvRow
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
-    const int nstrips = (nx + OX - 1) / OX;
-    const int strip = (int)(blockIdx.x % (unsigned)nstrips);
-    const int y0 = (int)(blockIdx.x / (unsigned)nstrips) * seg;
-    const int rows = min(seg, ny - y0);           // output rows of this segment
     const int xs = strip * OX - (T - 1) + t;      // lattice column of slot t (unwrapped)
     const int x = wrap_slot<false>(xs, nx);
     const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
@@ -940,7 +940,6 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
         lrp = (I)wrap_inc(ly, ny) * nx;
     };
     // Residual check on level T: its snapshot entry is loaded one iteration ahead.
-    ResAcc<S> acc;
     ResSnap<S> so;
     auto snap_next = [&](int i) {
         so = snap_load<S>(a, n, (int64_t)((I)(ybeg + i - 2 * (T - 1)) * nx + xs));
@@ -1033,6 +1032,17 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
         i = 4 * m1;
     }
     for (; i < iters; ++i) iter(i, std::false_type{});
+}
+
+template <int S, bool GEN, int T, bool CHECK, typename I>
+__global__ void __launch_bounds__(kWvW, wv_minb<T>())
+k_wave(const StepParams a, const Coef<float> c, int seg) {
+    extern __shared__ float wv_ring[];            // (T-1) rings of 8 planes x kWvD rows x kWvRow
+    const int nstrips = (a.nx + wv_ox<T>() - 1) / wv_ox<T>();
+    const int strip = (int)(blockIdx.x % (unsigned)nstrips);
+    const int y0 = (int)(blockIdx.x / (unsigned)nstrips) * seg;
+    ResAcc<S> acc;
+    wave_block<S, GEN, T, CHECK, I>(a, c, wv_ring, strip, y0, min(seg, a.ny - y0), acc);
     if (CHECK) residual_reduce<S>(a, acc);
 }
 

@@ -262,11 +262,14 @@ int lbm_server_create(size_t hbm_budget_bytes, int check_every, lbm_server** out
             return set_last_error(rc, "lbm_server_create: " + err);
         }
     }
-    // two-step tiles by default (chunk length even), else 128-column tiles,
-    // unless the autotuner cache holds a choice for this chunk length
-    const bool even = check_every % 2 == 0;
+    // the wavefront chunk by default (chunk length a multiple of 4), else
+    // two-step tiles (even) or 128-column tiles, unless the autotuner cache
+    // holds a choice for this chunk length
+    const bool even = check_every % 2 == 0, four = check_every % 4 == 0;
     int v = autotune_lookup("server|k" + std::to_string(check_every));
-    s->tile_v = (v == 1 || v == 2 || v == 4 || (v == kTileTwoStep && even)) ? v : (even ? kTileTwoStep : 4);
+    s->tile_v = (v == 1 || v == 2 || v == 4 || (v == kTileTwoStep && even) || (v == kTileWave && four))
+                    ? v
+                    : (four ? kTileWave : (even ? kTileTwoStep : 4));
     lbm_server* raw = s.release();
     raw->worker = std::thread([raw] { raw->run(); });
     *out = raw;

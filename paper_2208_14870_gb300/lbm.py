@@ -283,6 +283,7 @@ def lbm_get_device_bytes(ctx: int) -> int:
 
 LBM_NOALLOC_MAX_BLOCKS = 1024
 LBM_TILE_TWO_STEP = 3
+LBM_TILE_WAVE = 5
 
 
 def lbm_step_checked_noalloc(nx: int, ny: int, lam: float, mu: float, dtype: int, f_src: int,

@@ -57,7 +57,7 @@ def test_batch_matches_single_lattice_and_fixed_point(dtype, tol, k, tol_fix):
     probs = make_problems(SIZES)
     results, report = P.batch_solve([p[:6] for p in probs], dtype=dtype, tol=tol,
                                     check_every=k, max_iters=2_000_000)
-    assert report["tile_v"] in (1, 2, 4, P.LBM_TILE_TWO_STEP) and report["chunks"] >= 4
+    assert report["tile_v"] in (1, 2, 4, P.LBM_TILE_TWO_STEP, P.LBM_TILE_WAVE) and report["chunks"] >= 4
     for (nx, ny, lam, mu, gx, gy, pw), r in zip(probs, results):
         assert r["status"] == P.LBM_OK, (nx, ny, r)
         rates = oracle.relaxation_rates(lam, mu)
@@ -113,27 +113,53 @@ def test_batch_rejects_bad_arguments():
         P.batch_solve(probs, check_every=1)
 
 
+# wide problems (from 256 columns and 8 rows) take wavefront items in the
+# wavefront chunk: one strip, several strips with a ragged last one, one row
+# of segments and several
+WIDE = [(256, 8), (300, 60), (517, 33), (1000, 150)]
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f16s"])
-def test_batch_two_step_tiles_match_one_step_tiles(dtype, monkeypatch):
+def test_batch_tile_codes_agree(dtype, monkeypatch):
     """Two-step arena tiles (two steps per tile visit, one grid barrier per
-    pair) against 128-column one-step tiles: FP32 bit for bit, with the same
+    pair) and the wavefront chunk (four steps per wavefront item of a wide
+    problem, two-step tiles for the narrow ones, two grid barriers per four
+    steps) against 128-column one-step tiles: FP32 bit for bit, with the same
     stopping step; FP16S within its storage tolerance.  The problems include
-    lattices smaller than the 64 x 24 on-chip tile."""
-    probs = make_problems(SIZES, seed=11)
+    lattices smaller than the 64 x 24 on-chip tile and wide ones."""
+    probs = make_problems(SIZES + WIDE, seed=11)
     out = {}
-    for v in (4, P.LBM_TILE_TWO_STEP):
+    for v in (4, P.LBM_TILE_TWO_STEP, P.LBM_TILE_WAVE):
         monkeypatch.setenv("LBM_BATCH_TILE_V", str(v))
         results, report = P.batch_solve([p[:6] for p in probs], dtype=dtype, tol=1e-6, check_every=100,
                                         max_iters=400_000)
         assert report["tile_v"] == v
         out[v] = results
-    for a, b in zip(out[4], out[P.LBM_TILE_TWO_STEP]):
-        assert a["status"] == b["status"] == P.LBM_OK
-        if dtype == "f32":
-            assert a["iters"] == b["iters"]
-            assert np.array_equal(a["fields"], b["fields"])
-        else:
-            assert rel_per_field(b["fields"], a["fields"]) < 2e-3
+    for v in (P.LBM_TILE_TWO_STEP, P.LBM_TILE_WAVE):
+        for a, b, pr in zip(out[4], out[v], probs):
+            assert a["status"] == b["status"] == P.LBM_OK, (v, pr[:2])
+            if dtype == "f32":
+                assert a["iters"] == b["iters"], (v, pr[:2])
+                assert np.array_equal(a["fields"], b["fields"]), (v, pr[:2])
+            else:
+                assert rel_per_field(b["fields"], a["fields"]) < 2e-3, (v, pr[:2])
+
+
+def test_batch_wavefront_chunk_matches_single_lattice(monkeypatch):
+    """The wavefront chunk against the single-lattice path on the same wide
+    and narrow problems, FP32, a fixed step count (no check stops): the same
+    bits."""
+    probs = make_problems(WIDE + [(64, 64), (33, 17)], seed=19)
+    monkeypatch.setenv("LBM_BATCH_TILE_V", str(P.LBM_TILE_WAVE))
+    results, report = P.batch_solve([p[:6] for p in probs], dtype="f32", tol=0.0, check_every=100,
+                                    max_iters=300)
+    assert report["tile_v"] == P.LBM_TILE_WAVE
+    for (nx, ny, lam, mu, gx, gy, pw), r in zip(probs, results):
+        assert r["status"] == P.LBM_ERR_NOT_CONVERGED and r["iters"] == 300
+        with P.Lattice(nx, ny, lam, mu, "f32") as lat:
+            lat.set_force(gx, gy)
+            lat.iterate(300)
+            assert np.array_equal(r["fields"], lat.fields()), (nx, ny)
 
 
 def test_batch_recovery_packs_small_and_large_problems():
