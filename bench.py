@@ -691,19 +691,25 @@ def run_batched(args, P):
     res, rep = P.batch_solve(plist, "f32", args.tol, args.check_every)
     tb = time.perf_counter() - t0
     ok = sum(1 for r in res if r["status"] == 0)
+    # the plain baseline: every plain_every-th problem of the same stream (an
+    # unbiased sample of its size and parameter distribution), one at a time
+    sample = probs[::args.batched_plain_every]
     t0 = time.perf_counter()
     iters = 0
-    for p in probs:
+    for p in sample:
         st, it = plain_solve(P, p, args.tol, args.check_every)
         iters += it
     tp = time.perf_counter() - t0
-    return {"workload": "config-4 stream (seed %#x), the %d problems with max side <= %d, FP32, "
+    return {"workload": "config-4 stream (seed %#x), %d problems with max side <= %d, FP32, "
                         "tol %g, residual every %d steps" % (0x5EED_BA7C4ED, len(probs),
                                                              args.batched_cap, args.tol,
                                                              args.check_every),
+            "max_side": max(max(p.nx, p.ny) for p in probs),
             "problems": len(probs), "converged": ok,
-            "solves_per_s": len(probs) / tb, "plain_solves_per_s": len(probs) / tp,
-            "speedup_vs_plain": tp / tb, "wall_s": tb, "plain_wall_s": tp,
+            "solves_per_s": len(probs) / tb, "plain_solves_per_s": len(sample) / tp,
+            "plain_sample": "every %d-th problem of the same stream (%d of %d), solved one at a time "
+                            "through lbm_solve" % (args.batched_plain_every, len(sample), len(probs)),
+            "speedup_vs_plain": (len(probs) / tb) / (len(sample) / tp), "wall_s": tb, "plain_wall_s": tp,
             "lattice_updates": rep["lattice_updates"],
             "glups_device": rep["lattice_updates"] / (rep["device_ms"] / 1e3) / 1e9,
             "tile_v": rep["tile_v"], "chunks": rep["chunks"], "blocks": rep["blocks"]}
@@ -716,6 +722,7 @@ def run_served(args, P):
     arriving at --served-rate requests/s, through lbm_server_*; compared with a
     single-server queue of plain lbm_solve calls on the same requests."""
     import threading
+    budget = int(args.served_budget_gb * 1e9)
     stream = W.served_requests(rate_hz=args.served_rate)
     picked = [i for i, r in enumerate(stream) if max(r.nx, r.ny) <= args.served_cap]
     picked = picked[:args.served_max]
@@ -728,7 +735,7 @@ def run_served(args, P):
         r.arrival = t_first + (r.arrival - t_first) * p_keep
     forces = [W.random_force_grid(r.force) for r in reqs]
     tickets = [None] * len(reqs)
-    with P.Server(int(150e9), check_every=args.check_every) as srv:
+    with P.Server(budget, check_every=args.check_every) as srv:
         start = time.perf_counter()
 
         def feeder():
@@ -758,11 +765,15 @@ def run_served(args, P):
     lat = np.array(lat)
     return {"workload": "config-5 stream (seed %#x): first %d requests with max side <= %d, "
                         "Poisson arrivals at %g req/s, tol %g, FP32/FP16S per request, "
-                        "150 GB budget" % (0x5E4FED, len(reqs), args.served_cap,
-                                           args.served_rate, args.tol),
+                        "HBM budget %g GB (each storage type's arena half of it)" % (
+                            0x5E4FED, len(reqs), args.served_cap, args.served_rate, args.tol,
+                            args.served_budget_gb),
             "requests": len(reqs), "converged": statuses.count(0),
+            "max_side": max(max(r.nx, r.ny) for r in reqs),
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"],
             "p99_ms": st["p99_ms"], "peak_running": st["peak_running"],
+            "budget_bytes": budget, "peak_resident_bytes": st["peak_resident_bytes"],
+            "memory_waits": st["memory_waits"],
             "device_s": st["device_ms"] / 1e3, "chunks": st["chunks"], "tile_v": st["tile_v"],
             "lattice_updates": st["lattice_updates"],
             "glups_device": st["lattice_updates"] / max(st["device_ms"], 1e-9) / 1e6,
@@ -805,12 +816,17 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--batched-cap", type=int, default=256)
+    ap.add_argument("--batched-cap", type=int, default=1024,
+                    help="longest side of the batched problems kept (1024: the whole stream)")
     ap.add_argument("--batched-max", type=int, default=2048)
+    ap.add_argument("--batched-plain-every", type=int, default=4,
+                    help="the plain one-at-a-time baseline solves every k-th problem of the batch")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--served-cap", type=int, default=256)
-    ap.add_argument("--served-max", type=int, default=300)
-    ap.add_argument("--served-rate", type=float, default=300.0)
+    ap.add_argument("--served-cap", type=int, default=2048)
+    ap.add_argument("--served-max", type=int, default=100)
+    ap.add_argument("--served-rate", type=float, default=20.0)
+    ap.add_argument("--served-budget-gb", type=float, default=4.0,
+                    help="HBM budget of the server (small enough that admission waits on memory)")
     ap.add_argument("--sweep-max-n", type=int, default=2048)
     ap.add_argument("--sweep-f64-max", type=int, default=512)
     ap.add_argument("--only", choices=["batched", "served", "sweep"], default=None,

@@ -149,7 +149,7 @@ int lbm_get_steps_per_launch(lbm_ctx *ctx, int *k);
  * columns per strip instead of a ring of nodes around every tile.  Same steps
  * and, for LBM_F32, the same bits as one step per launch (see
  * lbm_set_steps_per_launch).  Used where nx >= 256 and ny >= 8; smaller
- * lattices keep the tile schedule.  With rows = -1 a segment is 128 rows,
+ * lattices keep the tile schedule.  With rows = -1 a segment is 256 rows,
  * halved (down to 16) while the grid would have fewer than four waves of
  * resident blocks.  Default -1 for LBM_F32 and LBM_F16S storage, 0 for
  * LBM_F64.
@@ -159,7 +159,10 @@ int lbm_set_wavefront(lbm_ctx *ctx, int rows);
 int lbm_get_wavefront(lbm_ctx *ctx, int *rows);
 
 /* Body force (constant in pseudo-time, Sec. 2.1).  gx, gy: host arrays of
- * nx*ny doubles (lattice units), copied.  The force must be finite; the
+ * nx*ny doubles (lattice units), copied.  Pinned host arrays the device can
+ * address (cudaHostAlloc / cudaMallocHost, or registered mapped memory) are
+ * read by the conversion kernel directly over the host link; other host
+ * arrays go through a device staging copy.  The force must be finite; the
  * steady state exists for a zero-mean force (the mean of u is conserved,
  * Sec. 6.2), which is the caller's responsibility.  For LBM_F16S a change of
  * the force magnitude rescales the stored deviations.  Synchronous. */
@@ -260,11 +263,15 @@ int lbm_solve(lbm_ctx *ctx, double tol, int64_t max_iters, int check_every,
               int64_t *iters_out, double *residual_out);
 
 /* Displacement u_x = mbar_10, u_y = mbar_01 (Table 2, Eq. coll10) of the
- * current state, FP64, into host arrays of nx*ny doubles.  Synchronous. */
+ * current state, FP64, into host arrays of nx*ny doubles.  Pinned host arrays
+ * the device can address are written by the recovery kernel directly; into
+ * other host arrays the fields are copied from a device staging buffer (one
+ * recovery per state, shared with lbm_get_stress).  Synchronous. */
 int lbm_get_displacement(lbm_ctx *ctx, double *ux, double *uy);
 
 /* Cauchy stress in lattice units (Table 2 times eps, Eq. compute_bared with
- * the Table 1 equilibria), FP64, into host arrays of nx*ny.  Synchronous. */
+ * the Table 1 equilibria), FP64, into host arrays of nx*ny (pinned host
+ * arrays written directly, as for lbm_get_displacement).  Synchronous. */
 int lbm_get_stress(lbm_ctx *ctx, double *sxx, double *syy, double *sxy);
 
 /* All five fields (u_x, u_y, sigma_xx, sigma_yy, sigma_xy) into a device
@@ -388,6 +395,9 @@ typedef struct lbm_stats {
     int peak_running;          /* most problems resident at once */
     int tile_v;                /* tile code: 1, 2, 4 (warps of 32 columns), LBM_TILE_TWO_STEP or LBM_TILE_WAVE */
     int failed;                /* LBM_OK, or the error that stopped the worker */
+    int64_t memory_waits;      /* admission attempts refused because the request's arena lacked
+                                  free memory (one per queued request and chunk) */
+    size_t peak_resident_bytes;/* most arena memory held by resident problems at once (both arenas) */
 } lbm_stats;
 
 /* Start a server on the current device with an HBM budget (bytes, >= 1 MiB)

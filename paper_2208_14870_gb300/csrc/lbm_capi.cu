@@ -278,7 +278,7 @@ cudaError_t run_window(lbm_ctx* c, int64_t to_check) {
     return e == cudaSuccess ? launch_step(c, true) : e;
 }
 
-cudaError_t launch_fields(lbm_ctx* c, double* out);
+cudaError_t launch_fields(lbm_ctx* c, const FieldOut& out);
 int ensure_staging(lbm_ctx* c, int64_t len);
 
 // The five FP64 field planes of the current state in the staging buffer,
@@ -288,12 +288,12 @@ int stage_fields(lbm_ctx* c) {
     if (c->staged_fields) return LBM_OK;
     int rc = ensure_staging(c, 5 * c->n);
     if (rc) return rc;
-    CK(launch_fields(c, c->staging));
+    CK(launch_fields(c, field_planes(c->staging, c->n)));
     c->staged_fields = true;
     return LBM_OK;
 }
 
-cudaError_t launch_fields(lbm_ctx* c, double* out) {
+cudaError_t launch_fields(lbm_ctx* c, const FieldOut& out) {
     const StepParams a = params(c, c->cur);
     const Coef<double> cd = coef<double>(c->rates);
     switch (c->dtype) {
@@ -379,10 +379,20 @@ int set_half_exponent(lbm_ctx* c, int e, bool rescale) {
     return LBM_OK;
 }
 
-int update_half_scale(lbm_ctx* c, const double* gx_dev, const double* gy_dev) {
+// The force in the storage type from FP64 arrays the device can address
+// (device memory, or mapped pinned host memory), in one pass that also finds
+// max |g| and non-finite entries; then the FP16 scale.
+int set_force_dev(lbm_ctx* c, const double* gx, const double* gy) {
+    c->staged_fields = false;
     CK(cudaMemsetAsync(c->absmax, 0, sizeof(unsigned long long), c->stream));
     CK(cudaMemsetAsync(c->bad, 0, sizeof(unsigned int), c->stream));
-    k_absmax<<<1024, 256, 0, c->stream>>>(gx_dev, gy_dev, c->n, c->absmax, c->bad);
+    if (c->dtype == LBM_F64) {
+        double* fx = static_cast<double*>(c->force);
+        k_force_ingest<double><<<2048, 256, 0, c->stream>>>(gx, gy, fx, fx + c->plane, c->n, c->absmax, c->bad);
+    } else {
+        float* fx = static_cast<float*>(c->force);
+        k_force_ingest<float><<<2048, 256, 0, c->stream>>>(gx, gy, fx, fx + c->plane, c->n, c->absmax, c->bad);
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->pinned, c->absmax, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(c->pinned + 1, c->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost,
@@ -402,19 +412,15 @@ int update_half_scale(lbm_ctx* c, const double* gx_dev, const double* gy_dev) {
     return set_half_exponent(c, e, !c->state_zero);
 }
 
-int set_force_dev(lbm_ctx* c, const double* gx, const double* gy) {
-    c->staged_fields = false;
-    if (c->dtype == LBM_F64) {
-        CK(cudaMemcpyAsync(c->force, gx, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        CK(cudaMemcpyAsync(static_cast<double*>(c->force) + c->plane, gy, c->n * sizeof(double),
-                           cudaMemcpyDeviceToDevice, c->stream));
-    } else {
-        float* fx = static_cast<float*>(c->force);
-        k_force_convert<float><<<2048, 256, 0, c->stream>>>(gx, gy, fx, fx + c->plane, c->n);
-        CK(cudaGetLastError());
+// The device address of a host buffer that is pinned and mapped (then the
+// device reads or writes it over the host link directly), or null.
+const void* mapped_host(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // an unregistered pointer is not an error here
+        return nullptr;
     }
-    // validates the force (finite) for every storage type; picks the FP16 scale
-    return update_half_scale(c, gx, gy);
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 // Reads the residual of the last check; returns r_inf etc. in out[0..4].
@@ -619,15 +625,16 @@ int lbm_set_force(lbm_ctx* c, const double* gx, const double* gy) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!gx || !gy) return fail(LBM_ERR_ARG, "lbm_set_force: null pointer");
+    // pinned, mapped host arrays: read by the conversion kernel directly
+    const void* mx = mapped_host(gx);
+    const void* my = mapped_host(gy);
+    if (mx && my) return set_force_dev(c, static_cast<const double*>(mx), static_cast<const double*>(my));
     rc = ensure_staging(c, 2 * c->n);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->staging, gx, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->staging + c->n, gy, c->n * sizeof(double), cudaMemcpyHostToDevice,
                        c->stream));
-    rc = set_force_dev(c, c->staging, c->staging + c->n);
-    if (rc) return rc;
-    CK(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    return set_force_dev(c, c->staging, c->staging + c->n);
 }
 
 int lbm_set_force_corrected(lbm_ctx* c, const double* gx, const double* gy, const double* d) {
@@ -645,10 +652,7 @@ int lbm_set_force_corrected(lbm_ctx* c, const double* gx, const double* gy, cons
     k_force_correct<<<1024, 256, 0, c->stream>>>(in, in + c->n, out, out + c->n, c->nx, c->ny, d[0],
                                                  d[1], d[2]);
     CK(cudaGetLastError());
-    rc = set_force_dev(c, out, out + c->n);
-    if (rc) return rc;
-    CK(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    return set_force_dev(c, out, out + c->n);
 }
 
 namespace {
@@ -861,35 +865,52 @@ int lbm_get_fields_device(lbm_ctx* c, double* out) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!out) return fail(LBM_ERR_ARG, "lbm_get_fields_device: null pointer");
-    CK(launch_fields(c, out));
+    CK(launch_fields(c, field_planes(out, c->n)));
     return LBM_OK;
 }
+
+namespace {
+
+// Host field getters: into pinned, mapped host arrays the recovery kernel
+// writes directly (only the requested fields); other host arrays receive
+// copies of the fields staged once per state.
+int get_fields_host(lbm_ctx* c, int first, int count, double* const* dst) {
+    FieldOut o{};
+    bool mapped = true;
+    for (int k = 0; k < count && mapped; ++k) {
+        o.p[first + k] = static_cast<double*>(const_cast<void*>(mapped_host(dst[k])));
+        mapped = o.p[first + k] != nullptr;
+    }
+    if (mapped) {
+        CK(launch_fields(c, o));
+        CK(cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+    int rc = stage_fields(c);
+    if (rc) return rc;
+    for (int k = 0; k < count; ++k)
+        CK(cudaMemcpyAsync(dst[k], c->staging + (first + k) * c->n, c->n * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+}  // namespace
 
 int lbm_get_displacement(lbm_ctx* c, double* ux, double* uy) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!ux || !uy) return fail(LBM_ERR_ARG, "lbm_get_displacement: null pointer");
-    rc = stage_fields(c);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(ux, c->staging, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(uy, c->staging + c->n, c->n * sizeof(double), cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    double* d[2] = {ux, uy};
+    return get_fields_host(c, 0, 2, d);
 }
 
 int lbm_get_stress(lbm_ctx* c, double* sxx, double* syy, double* sxy) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!sxx || !syy || !sxy) return fail(LBM_ERR_ARG, "lbm_get_stress: null pointer");
-    rc = stage_fields(c);
-    if (rc) return rc;
-    double* outs[3] = {sxx, syy, sxy};
-    for (int k = 0; k < 3; ++k)
-        CK(cudaMemcpyAsync(outs[k], c->staging + (2 + k) * c->n, c->n * sizeof(double),
-                           cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    double* d[3] = {sxx, syy, sxy};
+    return get_fields_host(c, 2, 3, d);
 }
 
 int lbm_get_populations(lbm_ctx* c, double* f) {

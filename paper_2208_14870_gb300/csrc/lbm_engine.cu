@@ -214,6 +214,13 @@ int64_t ArenaEngine::running_nodes() const {
     return t;
 }
 
+int64_t ArenaEngine::resident_bytes() const {
+    int64_t b = 0;
+    for (const auto& p : probs_)
+        if (p.state != P_FREE) b += bytes_for(p.n);
+    return b;
+}
+
 int ArenaEngine::grid_blocks(int V) const { return arena_occupancy(dtype_, V) * sms_; }
 
 int64_t ArenaEngine::free_nodes_hint() const {
@@ -449,8 +456,8 @@ cudaError_t ArenaEngine::launch_fields(int slot, double* dst) {
     c.bs = 1.0 - 0.5 * ws;
     c.bd = 1.0 - 0.5 * wd;
     c.theta = theta;
-    return dtype_ == S_F16S ? Ops<S_F16S>::fields(a, c, (float)theta, dst, st_)
-                            : Ops<S_F32>::fields(a, c, (float)theta, dst, st_);
+    return dtype_ == S_F16S ? Ops<S_F16S>::fields(a, c, (float)theta, field_planes(dst, p.n), st_)
+                            : Ops<S_F32>::fields(a, c, (float)theta, field_planes(dst, p.n), st_);
 }
 
 int ArenaEngine::ensure_fields_buffer(int64_t len, std::string* err) {

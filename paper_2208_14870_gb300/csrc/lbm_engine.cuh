@@ -66,6 +66,8 @@ public:
     int running() const { return nrunning_; }
     int64_t running_tiles(int V) const;
     int64_t running_nodes() const;
+    // Arena bytes held by admitted problems (running or finished, not released).
+    int64_t resident_bytes() const;
     int max_probs() const { return (int)probs_.size(); }
     int grid_blocks(int V) const;
     int64_t free_nodes_hint() const;

@@ -1046,11 +1046,24 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
     if (CHECK) residual_reduce<S>(a, acc);
 }
 
-// Solution fields of the current state (Table 2, Eq. compute_bared), FP64:
-// out planes u_x, u_y, sigma_xx, sigma_yy, sigma_xy (stride nx*ny).
+// Destinations of the five solution fields u_x, u_y, sigma_xx, sigma_yy,
+// sigma_xy (nx*ny doubles each; a null entry is not written).  Device memory,
+// or pinned host memory the device can address (the recovery then writes the
+// caller's arrays over the host link directly).
+struct FieldOut {
+    double* p[5];
+};
+
+inline FieldOut field_planes(double* out, int64_t n) {
+    FieldOut o;
+    for (int k = 0; k < 5; ++k) o.p[k] = out + k * n;
+    return o;
+}
+
+// Solution fields of the current state (Table 2, Eq. compute_bared), FP64.
 template <int S>
 __global__ void __launch_bounds__(kThreads)
-k_fields(const StepParams a, const Coef<double> c, typename StoreT<S>::T theta, double* out) {
+k_fields(const StepParams a, const Coef<double> c, typename StoreT<S>::T theta, const FieldOut out) {
     using T = typename StoreT<S>::T;
     using G = typename StoreT<S>::G;
     const int nx = a.nx, ny = a.ny;
@@ -1068,12 +1081,13 @@ k_fields(const StepParams a, const Coef<double> c, typename StoreT<S>::T theta, 
     const int64_t idx = r0 + x, n = (int64_t)nx * ny;
     const double gx = double(static_cast<const G*>(a.gx)[idx]);
     const double gy = double(static_cast<const G*>(a.gy)[idx]);
+    (void)n;
     const double mb11 = c.b11 * m.m11, mbs = c.bs * m.ms, mbd = c.bd * m.md;
-    out[idx] = m.m10 + 0.5 * gx;
-    out[n + idx] = m.m01 + 0.5 * gy;
-    out[2 * n + idx] = -0.5 * (mbs + mbd);
-    out[3 * n + idx] = -0.5 * (mbs - mbd);
-    out[4 * n + idx] = -mb11;
+    if (out.p[0]) out.p[0][idx] = m.m10 + 0.5 * gx;
+    if (out.p[1]) out.p[1][idx] = m.m01 + 0.5 * gy;
+    if (out.p[2]) out.p[2][idx] = -0.5 * (mbs + mbd);
+    if (out.p[3]) out.p[3][idx] = -0.5 * (mbs - mbd);
+    if (out.p[4]) out.p[4][idx] = -mb11;
 }
 
 // Pre-collision populations of the current state into 8 FP64 planes.
@@ -1133,21 +1147,34 @@ k_import(const StepParams a, typename StoreT<S>::T theta, const double* in) {
     }
 }
 
-// Force upload: FP64 device arrays -> storage force type.
+// Force upload in one pass over the FP64 input (device memory, or pinned host
+// memory the device can address): the force in the storage force type G, its
+// max |g| over both components (non-negative doubles order like their bit
+// patterns, so an unsigned 64-bit atomicMax suffices) and `bad` set by a
+// non-finite entry.
 template <typename G>
-__global__ void k_force_convert(const double* gx, const double* gy, G* ox, G* oy, int64_t n) {
+__global__ void k_force_ingest(const double* gx, const double* gy, G* ox, G* oy, int64_t n,
+                               unsigned long long* absmax, unsigned int* bad) {
+    double m = 0.0;
+    unsigned int b = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        ox[i] = G(gx[i]);
-        oy[i] = G(gy[i]);
+        const double u = gx[i], v = gy[i];
+        ox[i] = G(u);
+        oy[i] = G(v);
+        if (!(isfinite(u) && isfinite(v))) b = 1;
+        m = fmax(m, fmax(fabs(u), fabs(v)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        b |= __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(absmax, (unsigned long long)__double_as_longlong(m));
+        if (b) atomicOr(bad, 1u);
     }
 }
-
-// max |g| over both force components (non-negative doubles order like their
-// bit patterns, so an unsigned 64-bit atomicMax suffices).  A non-finite
-// entry sets `bad`.
-__global__ void k_absmax(const double* gx, const double* gy, int64_t n,
-                         unsigned long long* out, unsigned int* bad);
 
 // F16S: multiply every stored deviation by `factor` (a power of two).
 __global__ void k_rescale_half(__half* h, int64_t count, float factor);
@@ -1170,7 +1197,7 @@ struct Ops {
     // block per tile below it
     static cudaError_t step(const StepParams& a, const Coef<T>& c, int V, bool gen, bool check,
                             int check_blocks, cudaStream_t st);
-    static cudaError_t fields(const StepParams& a, const Coef<double>& c, T theta, double* out,
+    static cudaError_t fields(const StepParams& a, const Coef<double>& c, T theta, const FieldOut& out,
                               cudaStream_t st);
     static cudaError_t export_pop(const StepParams& a, T theta, double* out, cudaStream_t st);
     static cudaError_t import_pop(const StepParams& a, T theta, const double* in, cudaStream_t st);

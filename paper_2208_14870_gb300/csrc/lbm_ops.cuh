@@ -182,7 +182,7 @@ cudaError_t Ops<S>::step(const StepParams& a, const Coef<T>& c, int V, bool gen,
 }
 
 template <int S>
-cudaError_t Ops<S>::fields(const StepParams& a, const Coef<double>& c, T theta, double* out,
+cudaError_t Ops<S>::fields(const StepParams& a, const Coef<double>& c, T theta, const FieldOut& out,
                            cudaStream_t st) {
     k_fields<S><<<step_grid(a.nx, a.ny, 1), dim3(32, BY), 0, st>>>(a, c, theta, out);
     return cudaGetLastError();

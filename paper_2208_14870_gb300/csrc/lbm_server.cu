@@ -88,6 +88,8 @@ struct lbm_server {
     int64_t submitted = 0, completed = 0, chunks = 0, lups = 0;
     double device_ms = 0.0;
     int peak_running = 0;
+    int64_t memory_waits = 0;
+    int64_t peak_resident = 0;
     std::vector<double> latencies_ms;
     bool any_submit = false;
     clk::time_point t_first_submit, t_last_done;
@@ -108,6 +110,7 @@ void lbm_server::run() {
         }
         const int r0 = arena[0]->running(), r1 = arena[1]->running();
         peak_running = std::max(peak_running, r0 + r1);
+        peak_resident = std::max(peak_resident, arena[0]->resident_bytes() + arena[1]->resident_bytes());
         if (r0 + r1 == 0) {
             cv_work.wait_for(lk, std::chrono::milliseconds(50));
             continue;
@@ -181,6 +184,7 @@ int lbm_server::admit_locked() {
             continue;
         }
         if (s < -1) return s;  // a real error
+        ++memory_waits;
         if (r.bypassed > max_bypass_chunks) blocked[a] = true;
         ++it;
     }
@@ -409,6 +413,8 @@ int lbm_server_stats(lbm_server* s, lbm_stats* out) {
     out->chunks = s->chunks;
     out->hbm_bytes = (size_t)(s->arena[0]->device_bytes() + s->arena[1]->device_bytes());
     out->peak_running = s->peak_running;
+    out->memory_waits = s->memory_waits;
+    out->peak_resident_bytes = (size_t)s->peak_resident;
     out->tile_v = s->tile_v;
     out->failed = s->failed;
     return LBM_OK;

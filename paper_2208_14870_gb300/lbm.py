@@ -543,7 +543,8 @@ class lbm_stats(ctypes.Structure):
                 ("solves_per_s", ctypes.c_double), ("lattice_updates", ctypes.c_int64),
                 ("device_ms", ctypes.c_double), ("chunks", ctypes.c_int64),
                 ("hbm_bytes", ctypes.c_size_t), ("peak_running", ctypes.c_int),
-                ("tile_v", ctypes.c_int), ("failed", ctypes.c_int)]
+                ("tile_v", ctypes.c_int), ("failed", ctypes.c_int),
+                ("memory_waits", ctypes.c_int64), ("peak_resident_bytes", ctypes.c_size_t)]
 
 
 for _name, _res, _args in (

@@ -386,3 +386,37 @@ def test_host_field_getters_follow_every_state_change():
         assert np.allclose(z[0], 0.25 * gx) and np.max(np.abs(z[2:])) == 0.0
         lat.set_populations(f)
         assert np.array_equal(check(), c)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_pinned_and_pageable_host_buffers_agree(dtype):
+    """lbm_set_force reads pinned host arrays with the conversion kernel over
+    the host link, and the field getters write pinned host arrays from the
+    recovery kernel; pageable arrays go through device staging copies.  Both
+    routes give the same bits, and a non-finite entry is rejected on both."""
+    lam, mu = W.lame_2d(1.0, 0.3)
+    nx, ny = 300, 70
+    pw = W.random_force(nx, ny, 6, 4, seed=99)
+    gx, gy = W.random_force_grid(pw)
+    pgx = torch.from_numpy(gx.copy()).pin_memory()
+    pgy = torch.from_numpy(gy.copy()).pin_memory()
+    out = []
+    for pinned in (False, True):
+        with Lattice(nx, ny, lam, mu, dtype) as lat:
+            if pinned:
+                P.lbm_set_force(lat.ctx, pgx.data_ptr(), pgy.data_ptr())
+            else:
+                P.lbm_set_force(lat.ctx, gx.ctypes.data, gy.ctypes.data)
+            lat.iterate(37)
+            if pinned:
+                f = [torch.empty(nx * ny, dtype=torch.float64).pin_memory() for _ in range(5)]
+                P.lbm_get_displacement(lat.ctx, f[0].data_ptr(), f[1].data_ptr())
+                P.lbm_get_stress(lat.ctx, f[2].data_ptr(), f[3].data_ptr(), f[4].data_ptr())
+                out.append(np.stack([t.numpy().reshape(ny, nx) for t in f]))
+            else:
+                out.append(np.concatenate([lat.displacement(), lat.stress()]))
+            bad = pgx.clone().pin_memory()
+            bad[5] = float("nan")
+            with pytest.raises(P.LBMError):
+                P.lbm_set_force(lat.ctx, bad.data_ptr(), pgy.data_ptr())
+    assert np.array_equal(out[0], out[1])

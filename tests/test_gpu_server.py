@@ -119,6 +119,9 @@ def test_budget_limits_residency_and_queue_drains():
     assert all(r["status"] == P.LBM_OK for r in rs)
     assert 1 <= st["peak_running"] <= 3
     assert st["completed"] == 12 and st["p99_ms"] >= st["p50_ms"] > 0
+    # admission waited on memory, and the resident problems never exceeded the budget
+    assert st["memory_waits"] > 0
+    assert 0 < st["peak_resident_bytes"] <= 8 << 20
 
 
 def test_host_side_faults():
