@@ -675,6 +675,31 @@ def run_sweep(args, P):
             "eps": eps, "rows": rows}
 
 
+def run_jitter(args, P):
+    """Rounding floor of the steady-state residual (reading c6b): a state
+    iterated far past convergence (e^-40 of its slowest mode) keeps jittering;
+    max|u^t - u^(t-w)| / max|u^t| over windows of w steps, three windows each,
+    FP32 and FP16S, N = 64, 256, 1024, random 8-mode force, nu = 0.3."""
+    rows = []
+    for dtype in ("f32", "f16s"):
+        for n in (64, 256, 1024):
+            lam, mu = W.lame_2d(1.0, 0.3)
+            pw = W.random_force(n, n, 8, 4, seed=7 + n)
+            gx, gy = W.random_force_grid(pw)
+            a = 2.0 * np.pi / n
+            steps = int(40.0 / (mu * a * a))
+            with P.Lattice(n, n, lam, mu, dtype) as lat:
+                lat.set_force(gx, gy)
+                lat.iterate(steps - steps % 100)
+                for w in (100, 1000, 6000):
+                    js = [float(lat.iterate_checked(2 * w, w)[0] * w) for _ in range(3)]
+                    rows.append({"dtype": dtype, "n": n, "window": w, "jitter": js})
+                    print("jitter %-4s N=%5d w=%5d %s" % (dtype, n, w, " ".join("%.2e" % j for j in js)),
+                          file=sys.stderr, flush=True)
+    return {"workload": "rounding floor of the residual: random 8-mode force, nu = 0.3, state iterated e^-40 "
+                        "past convergence, max|u^t - u^(t-w)| / max|u^t| per window", "rows": rows}
+
+
 def run_batched(args, P):
     """Config-4 stream (2048 problems, sides log-uniform in [32, 1024], nu in
     [0, 0.45], 8 random force modes, FP32, tol 1e-8): the problems whose longer
@@ -829,7 +854,7 @@ def main():
                     help="HBM budget of the server (small enough that admission waits on memory)")
     ap.add_argument("--sweep-max-n", type=int, default=2048)
     ap.add_argument("--sweep-f64-max", type=int, default=512)
-    ap.add_argument("--only", choices=["batched", "served", "sweep"], default=None,
+    ap.add_argument("--only", choices=["batched", "served", "sweep", "jitter"], default=None,
                     help="run one secondary workload alone and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -839,7 +864,8 @@ def main():
         import torch
         torch.cuda.set_device(local)
         import paper_2208_14870_gb300 as P
-        out = {"batched": run_batched, "served": run_served, "sweep": run_sweep}[args.only](args, P)
+        out = {"batched": run_batched, "served": run_served, "sweep": run_sweep,
+               "jitter": run_jitter}[args.only](args, P)
         print(json.dumps({"only": args.only, **out}), flush=True)
         return
     if args.impl == "reference":

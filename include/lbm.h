@@ -354,10 +354,12 @@ typedef struct lbm_batch_report {
 /* Solve `count` problems to residual tol (checked every check_every >= 2
  * steps; a problem stops at the first check below tol, at divergence, or at
  * the first check at or beyond max_iters steps).  Rounding keeps a stored
- * state jittering by about J |u| (J ~ 2e-7 for FP32, 3e-5 for FP16-shifted,
- * measured), which floors a w-step residual near J / w; a problem whose tol
- * is below that for w = check_every is checked over windows of
- * check_every * max(1, ceil(2 J / (tol * check_every))) steps instead.  dtype: LBM_F32 or LBM_F16S.
+ * state jittering by about J |u| (measured on converged states: J ~ 1.4e-7 to
+ * 4.3e-7 for FP32; for FP16-shifted storage about 3e-4 / N, N = max(nx, ny)),
+ * which floors a w-step residual near J / w; a problem whose tol is below that
+ * for w = check_every is checked over windows of check_every * min(64, max(1,
+ * ceil(2 J / (tol * check_every)))) steps instead, with J = 4e-7 (FP32) or
+ * 6e-4 / N (FP16S).  dtype: LBM_F32 or LBM_F16S.
  * results[i] receives status, steps, residual and, where the pointers are
  * non-null, the FP64 displacement and stress (Table 2).  report may be null.
  * Synchronous.  Returns LBM_OK when every problem was run (per-problem

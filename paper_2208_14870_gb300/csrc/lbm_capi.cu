@@ -819,7 +819,7 @@ int lbm_solve(lbm_ctx* c, double tol, int64_t max_iters, int check_every, int64_
         return fail(LBM_ERR_ARG, "lbm_solve: bad tol, max_iters or check_every");
     if (max_iters > 0) c->state_zero = false;
     // windows long enough that the storage's rounding jitter stays below tol
-    check_every *= check_period(c->dtype, tol, check_every);
+    check_every *= check_period(c->dtype, tol, check_every, std::max(c->nx, c->ny));
     int64_t done = 0;
     double r = INFINITY;
     int status = LBM_ERR_NOT_CONVERGED;

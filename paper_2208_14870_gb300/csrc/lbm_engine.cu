@@ -191,7 +191,7 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
     p.hexp = dtype_ == S_F16S ? f16s_exponent(gmax, nx, ny) : 0;
     p.tol = tol;
     p.max_iters = max_iters;
-    p.period = check_period(dtype_, tol, k_);
+    p.period = check_period(dtype_, tol, k_, std::max(nx, ny));
     p.state = P_RUNNING;
     probs_[slot] = p;
     ++nrunning_;

@@ -872,15 +872,22 @@ k_step3(const StepParams a, const Coef<float> c) {
 #ifndef LBM_WV_NW
 #define LBM_WV_NW 8
 #endif
-#ifndef LBM_WV_PREF2
-#define LBM_WV_PREF2 0
+// level-1 look-ahead per storage type: two rows ahead (1) or one (0); the
+// defaults are the faster of the two at 16384^2 on GB300 (FP32 3.63 against
+// 3.71 ms per four-step launch, FP16S 4.01 against 4.08 ms with one row)
+#ifndef LBM_WV_PREF2_F32
+#define LBM_WV_PREF2_F32 1
+#endif
+#ifndef LBM_WV_PREF2_F16S
+#define LBM_WV_PREF2_F16S 0
 #endif
 constexpr int kWvNW = LBM_WV_NW;                 // warps per block
 constexpr int kWvW = 32 * kWvNW;                 // strip width (slot columns)
 constexpr int kWvRow = kWvW + 2;                 // ring row: the strip plus one pad column per side
 constexpr int kWvD = 4;                          // ring rows per level
 constexpr int kWvSegDefault = 256;               // output rows per block segment (default)
-constexpr bool kWvPref2 = LBM_WV_PREF2 != 0;     // level-1 loads two rows ahead (else one)
+template <int S>
+__host__ __device__ constexpr bool wv_pref2() { return S == S_F16S ? LBM_WV_PREF2_F16S != 0 : LBM_WV_PREF2_F32 != 0; }
 static_assert(kWvW <= kThreads, "residual_reduce sizes its scratch by kThreads");
 template <int T> __host__ __device__ constexpr int wv_ox() { return kWvW - 2 * (T - 1); }
 template <int T> __host__ __device__ constexpr int wv_smem() { return (T - 1) * 8 * kWvD * kWvRow * (int)sizeof(float); }
@@ -901,6 +908,7 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
                                            int strip, int y0, int rows, ResAcc<S>& acc) {
     static_assert(T >= 2 && T <= 4, "two to four steps per launch");
     constexpr int W = kWvW, R = kWvRow, OX = wv_ox<T>(), PL = kWvD * kWvRow, RP = 8 * PL, D = kWvD - 1;
+    constexpr bool kWvPref2 = wv_pref2<S>();
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
     const int xs = strip * OX - (T - 1) + t;      // lattice column of slot t (unwrapped)
@@ -922,9 +930,9 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     float hx[NH], hy[NH];
 #pragma unroll
     for (int k = 0; k < NH; ++k) hx[k] = hy[k] = 0.0f;
-    // Level 1 reads global memory one (LBM_WV_PREF2: two) rows ahead, so its
-    // loads are in flight while the iterations before work from shared
-    // memory.  The row offsets of the next row to load advance one row per
+    // Level 1 reads global memory two rows ahead (FP16S, whose pulls hold
+    // three times the registers: one), so its loads are in flight while the
+    // iterations before work from shared memory.  The row offsets of the next row to load advance one row per
     // load (rows are loaded in order), with the periodic wrap.
     Pulled<S> q[kWvPref2 ? 2 : 1];
     float qg[kWvPref2 ? 2 : 1][2];
@@ -950,10 +958,11 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     // of a level compute values no valid slot reads (their pulls stay inside
     // the padded ring rows), so no level branches per thread; only the
     // stores of level T are predicated.
-    auto iter = [&](int i, auto full_c) {
+    auto iter = [&](int i, auto full_c, auto buf_c) {
         constexpr bool FULL = decltype(full_c)::value;
+        constexpr int b = decltype(buf_c)::value;   // load buffer of local row i (i mod 2 with
+                                                    // two rows ahead, else 0)
         const bool l1 = FULL || i < n1;
-        const int b = kWvPref2 ? (i & 1) : 0;     // load buffer of local row i
 #pragma unroll
         for (int k = NH - 1; k > 0; --k) {
             hx[k] = hx[k - 1];
@@ -1019,19 +1028,25 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     const int fe = rows + 2 * T - 3 - (kWvPref2 ? 2 : 1);
     if (CHECK && store_ok) snap_next(fb);         // level T's first row is y0
     const int m0 = (fb + 3) >> 2, m1 = (fe + 1) >> 2;   // groups i = 4m .. 4m + 3 within [fb, fe]
+    using B0 = std::integral_constant<int, 0>;
+    using B1 = std::integral_constant<int, kWvPref2 ? 1 : 0>;
+    auto iter_any = [&](int i) {
+        if (kWvPref2 && (i & 1)) iter(i, std::false_type{}, B1{});
+        else iter(i, std::false_type{}, B0{});
+    };
     int i = 0;
     if (m1 > m0) {
-        for (; i < 4 * m0; ++i) iter(i, std::false_type{});
+        for (; i < 4 * m0; ++i) iter_any(i);
         for (int m = m0; m < m1; ++m) {
             const int ib = m << 2;
-            iter(ib, std::true_type{});
-            iter(ib + 1, std::true_type{});
-            iter(ib + 2, std::true_type{});
-            iter(ib + 3, std::true_type{});
+            iter(ib, std::true_type{}, B0{});
+            iter(ib + 1, std::true_type{}, B1{});
+            iter(ib + 2, std::true_type{}, B0{});
+            iter(ib + 3, std::true_type{}, B1{});
         }
         i = 4 * m1;
     }
-    for (; i < iters; ++i) iter(i, std::false_type{});
+    for (; i < iters; ++i) iter_any(i);
 }
 
 template <int S, bool GEN, int T, bool CHECK, typename I>
@@ -1215,14 +1230,18 @@ inline int f16s_exponent(double gmax, int nx, int ny) {
 }
 
 // Residual windows per check interval k: rounding keeps a stored state
-// jittering by about J |u| (J ~ 3e-15 for FP64, 2e-7 for FP32, 3e-5 for
-// FP16-shifted storage, measured), which floors a w-step residual near J / w;
-// a problem asking for tol is therefore checked every
-// min(64, max(1, ceil(2 J / (tol k)))) intervals of k steps.  The cap keeps
-// divergence detection (made at checks) within 64 intervals; a tol that would
-// need more is below what the storage type can resolve.
-inline int check_period(int dtype, double tol, int k) {
-    const double J = dtype == S_F16S ? 3e-5 : (dtype == S_F32 ? 2e-7 : 3e-15);
+// jittering by about J |u| (measured on converged states: J ~ 3e-15 for FP64,
+// 1.4e-7 .. 4.3e-7 for FP32, and for FP16-shifted storage about 3e-4 / N,
+// N = max(nx, ny), since its stored deviations are of size ~ u / N: 4e-6 at
+// N = 64, 8e-7 at 256, 2.5e-7 at 1024), which floors a w-step residual near
+// J / w; a problem asking for tol is therefore checked every
+// min(64, max(1, ceil(2 J / (tol k)))) intervals of k steps, with J = 4e-7
+// for FP32 and 6e-4 / N for FP16S (twice the measured values).  The cap
+// keeps divergence detection (made at checks) within 64 intervals; a tol
+// that would need more is below what the storage type can resolve.
+inline int check_period(int dtype, double tol, int k, int nmax) {
+    const double J = dtype == S_F16S ? 6e-4 / (double)(nmax > 1 ? nmax : 1)
+                                     : (dtype == S_F32 ? 4e-7 : 3e-15);
     if (!(tol > 0.0) || k < 1) return 64;
     const double p = ceil(2.0 * J / (tol * (double)k));
     return p < 1.0 ? 1 : (p > 64.0 ? 64 : (int)p);
