@@ -7,12 +7,13 @@ TEST INFRASTRUCTURE ONLY.  The oracle exists to check the CUDA library; only
 imports the library package.
 
 Parts:
-  * ``lbm_oracle.c`` (loaded here through ctypes): Algorithm 1 written out
-    node by node in plain C, FP64 -- moments (Eq. moments, Eq. replace_raw),
-    half forcing (Eqs. coll10/coll01 and coll10post/coll01post), Table 1
-    equilibria, relaxation (Eq. collision), back-transformation
-    (Eq. moments_post), streaming (Eq. streaming) with the periodic wrap of
-    Sec. 5.1, and the solution fields of Table 2.
+  * ``lbm_oracle.c`` (loaded here through ctypes): one pseudo-time step as
+    the composition of the defining equations, node by node in plain C, FP64
+    -- the raw-moment map (Eq. moments, Eq. replace_raw), the collision of
+    Eq. collision on the moments with the Table 1 equilibria and the force
+    split around it (Eqs. coll10/coll01 and coll10post/coll01post), the
+    populations from Eq. moments_post, streaming (Eq. streaming) with the
+    periodic wrap of Sec. 5.1 -- and the solution fields of Table 2.
   * this module: the relaxation rates tied to the Lame parameters (Table 1,
     Eqs. match11/matchd/matchs, Eq. relaxation_rate), the 2D material
     relations (Eq. material_relations), the pseudo-time loop to steady state
@@ -160,7 +161,7 @@ def fourth_order_taus_scheme(lam: float, mu: float, theta: float = THETA_STANDAR
 
 
 # ----------------------------------------------------------------------------
-# Algorithm 1 through the C oracle
+# The pseudo-time step through the C oracle
 # ----------------------------------------------------------------------------
 
 def zero_state(nx: int, ny: int, q: int = 8) -> np.ndarray:
@@ -171,8 +172,9 @@ def zero_state(nx: int, ny: int, q: int = 8) -> np.ndarray:
 
 def run(f: np.ndarray, gx: np.ndarray, gy: np.ndarray, rates: np.ndarray,
         nsteps: int = 1) -> np.ndarray:
-    """Advance pre-collision populations f[q, ny, nx] by ``nsteps`` steps of
-    Algorithm 1; returns a new array."""
+    """Advance pre-collision populations f[q, ny, nx] by ``nsteps`` pseudo-time
+    steps (collision of Eq. collision at every node, then Eq. streaming);
+    returns a new array."""
     q, ny, nx = f.shape
     fin = np.ascontiguousarray(f, dtype=np.float64)
     gx = np.ascontiguousarray(gx, dtype=np.float64)
@@ -189,7 +191,7 @@ def run(f: np.ndarray, gx: np.ndarray, gy: np.ndarray, rates: np.ndarray,
 
 
 def collide(f: np.ndarray, gx: np.ndarray, gy: np.ndarray, rates: np.ndarray) -> np.ndarray:
-    """Post-collision populations f* (collision stage of Algorithm 1 only)."""
+    """Post-collision populations f* (the per-node collision map only)."""
     q, ny, nx = f.shape
     fin = np.ascontiguousarray(f, dtype=np.float64)
     out = np.empty_like(fin)
@@ -257,7 +259,7 @@ def residual(u_now: np.ndarray, u_prev: np.ndarray, k: int) -> tuple[float, floa
 def solve(gx: np.ndarray, gy: np.ndarray, rates: np.ndarray, tol: float,
           check_every: int = 100, max_iters: int = 10_000_000, q: int = 8,
           f0: np.ndarray | None = None):
-    """Iterate Algorithm 1 from the zero state until the residual
+    """Iterate the pseudo-time step from the zero state until the residual
     (``residual``) drops below ``tol``.  Returns (f, iters, r_inf)."""
     ny, nx = gx.shape
     f = zero_state(nx, ny, q) if f0 is None else f0

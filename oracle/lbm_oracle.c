@@ -9,8 +9,14 @@
  * the benchmark may load it.  It shares no code, header, table or constant
  * with the CUDA path.
  *
- * Everything follows the paper's Algorithm 1 ("single time step") in the
- * paper's order and notation:
+ * One pseudo-time step is the composition of the paper's defining equations,
+ * applied node by node and then as a shift of every population plane:
+ *   f(t+1) = S (M^-1 C(M f(t), g)),
+ * with M the raw-moment map of Eq. moments (rewritten by Eq. replace_raw), C
+ * the collision of Eq. collision with the Table 1 equilibria and the force
+ * split symmetrically around it (Eqs. coll10, coll01, coll10post,
+ * coll01post), M^-1 the solution of Eq. moments_post, and S the streaming of
+ * Eq. streaming with the periodic wrap of Sec. 5.1.  The pieces:
  *   - populations f_ij, i,j in {-1,0,1}; the D2Q8 set drops the rest
  *     population f_00 (Sec. 3.3.2, remark on m_00); an optional ninth slot
  *     carries f_00 to show that it is inert;
@@ -130,8 +136,10 @@ static void node_moments(int q, const double *f, double m[9]) {
     if (q == 9) m[8] = raw[8];     /* m_00 */
 }
 
-/* The collision stage of Algorithm 1 at one node: f (pre-collision) and the
- * force (gx, gy) give f* (post-collision). */
+/* The per-node map f* = M^-1 C(M f, g): raw moments of the pre-collision
+ * populations, the collision of Eq. collision on the moment vector (Table 1
+ * equilibria; the force enters half before and half after, Eqs. coll10 and
+ * coll10post), and the post-collision populations from Eq. moments_post. */
 static void collide_node(int q, const double inv[9][9], const rates_t *w,
                          const double *f, double gx, double gy, double *fs) {
     double m[9];
@@ -178,8 +186,9 @@ static int wrap(int i, int n) {
 }
 
 /*
- * One or more pseudo-time steps (Algorithm 1: collision at every node, then
- * streaming).  f_in holds the pre-collision populations at step t; f_out
+ * One or more pseudo-time steps f(t+1) = S(M^-1 C(M f(t), g)): the per-node
+ * map at every node, then streaming (Eq. streaming).  f_in holds the
+ * pre-collision populations at step t; f_out
  * receives them at step t + nsteps.  `tmp` is caller-provided scratch of the
  * same size as f_in.  f_in and f_out may be the same array.
  * Returns 0 on success, -1 on bad arguments.
@@ -215,7 +224,7 @@ int oracle_run(int nx, int ny, int q, const double *f_in, const double *gx,
 
 /*
  * Collision only (no streaming) at every node: f_star = collide(f).  Used by
- * tests that look at one stage of Algorithm 1 at a time.
+ * tests that look at the collision map on its own.
  */
 int oracle_collide(int nx, int ny, int q, const double *f, const double *gx,
                    const double *gy, const double *wv, double *f_star) {
