@@ -1089,17 +1089,38 @@ k_fields(const StepParams a, const Coef<double> c, typename StoreT<S>::T theta, 
     const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
     T f[8];
     gather<S>(a, r0, rm, rp, x, wrap_dec(x, nx), wrap_inc(x, nx), f, theta);
-    double fd[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) fd[p] = double(f[p]);
-    const Mom<double> m = moments(fd);
-    const int64_t idx = r0 + x, n = (int64_t)nx * ny;
-    const double gx = double(static_cast<const G*>(a.gx)[idx]);
-    const double gy = double(static_cast<const G*>(a.gy)[idx]);
-    (void)n;
-    const double mb11 = c.b11 * m.m11, mbs = c.bs * m.ms, mbd = c.bd * m.md;
-    if (out.p[0]) out.p[0][idx] = m.m10 + 0.5 * gx;
-    if (out.p[1]) out.p[1][idx] = m.m01 + 0.5 * gy;
+    const int64_t idx = r0 + x;
+    const G gxs = static_cast<const G*>(a.gx)[idx], gys = static_cast<const G*>(a.gy)[idx];
+    double u, v, m11, ms, md;
+    if constexpr (S == S_F64) {
+        const Mom<double> m = moments(f);
+        u = m.m10 + 0.5 * gxs;
+        v = m.m01 + 0.5 * gys;
+        m11 = m.m11;
+        ms = m.ms;
+        md = m.md;
+    } else {
+        // FP32 populations: the moments as exact FP32 pairs (TwoSum), each
+        // joined in FP64 once -- GB300 issues FP64 at a small fraction of the
+        // FP32 rate, and this keeps the recovery's FP64 work to the joins and
+        // the products of Eq. compute_bared
+        const float4 w = exact_displacement(f, gxs, gys);
+        u = (double)w.x + (double)w.y;
+        v = (double)w.z + (double)w.w;
+        float ep, eq, e13, e24, e11, e22, ed, et, es;
+        const float p = two_sum(f[4], f[6], ep), q = two_sum(f[5], f[7], eq);
+        const float h11 = two_sum(p, -q, e11), h22 = two_sum(p, q, e22);
+        const float s13 = two_sum(f[0], f[2], e13), s24 = two_sum(f[1], f[3], e24);
+        const float hd = two_sum(s13, -s24, ed), ht = two_sum(s13, s24, et);
+        const float l22 = __fadd_rn(e22, __fadd_rn(ep, eq));
+        const float hs = two_sum(ht, 2.0f * h22, es);   // m_s = (f1+f3) + (f2+f4) + 2 m_22
+        m11 = (double)h11 + (double)__fadd_rn(e11, __fsub_rn(ep, eq));
+        md = (double)hd + (double)__fadd_rn(ed, __fsub_rn(e13, e24));
+        ms = (double)hs + (double)__fadd_rn(__fadd_rn(es, __fadd_rn(et, __fadd_rn(e13, e24))), 2.0f * l22);
+    }
+    const double mb11 = c.b11 * m11, mbs = c.bs * ms, mbd = c.bd * md;
+    if (out.p[0]) out.p[0][idx] = u;
+    if (out.p[1]) out.p[1][idx] = v;
     if (out.p[2]) out.p[2][idx] = -0.5 * (mbs + mbd);
     if (out.p[3]) out.p[3][idx] = -0.5 * (mbs - mbd);
     if (out.p[4]) out.p[4][idx] = -mb11;

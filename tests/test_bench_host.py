@@ -88,7 +88,8 @@ def test_dominant_block(bench):
 def test_kernel_hash_ignores_comments_but_not_code(bench, tmp_path):
     d = os.path.join(ROOT, "paper_2208_14870_gb300", "csrc")
     files = {n: open(os.path.join(d, n)).read()
-             for n in ("lbm_core.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_step_f32.cu", "lbm_step_f16s.cu")}
+             for n in ("lbm_core.cuh", "lbm_kernels.cuh", "lbm_ops.cuh", "lbm_step_f32.cu", "lbm_step_f16s.cu",
+                       "lbm_wave_f32.cu", "lbm_wave_f16s.cu")}
     base = bench.kernel_hash(lambda n: files[n])
     assert base == bench.kernel_hash()
     commented = dict(files)
@@ -98,6 +99,12 @@ def test_kernel_hash_ignores_comments_but_not_code(bench, tmp_path):
     changed["lbm_kernels.cuh"] = files["lbm_kernels.cuh"].replace("#define LBM_BY 8", "#define LBM_BY 4")
     assert changed["lbm_kernels.cuh"] != files["lbm_kernels.cuh"]
     assert bench.kernel_hash(lambda n: changed[n]) != base
+    # the field recovery is not part of the stream-collide kernels
+    later = dict(files)
+    later["lbm_kernels.cuh"] = files["lbm_kernels.cuh"].replace("if (out.p[4]) out.p[4][idx] = -mb11;",
+                                                                 "if (out.p[4]) out.p[4][idx] = -1.0 * mb11;")
+    assert later["lbm_kernels.cuh"] != files["lbm_kernels.cuh"]
+    assert bench.kernel_hash(lambda n: later[n]) == base
 
 
 def test_host_description(bench):
