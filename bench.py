@@ -53,29 +53,20 @@ FORCE_SEED = 0x2208_14870
 FP64_INSTR_PER_LUP = 42
 FP64_FLOPS_PER_LUP = 51
 FP64_PEAK_GINST = 625.0
-# DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype
-# and steps per launch,
-# with the hash of the kernel code it was taken on (null once the code changes;
-# comments do not count).
-# Captured on 4096^2 (profiles/k_step*_4096_full.md) and scaled by the node
-# count (x16) to a 16384^2 launch; writes still dirty in L2 at the end of the
-# small launch are not counted, so these slightly undercount.
+# DRAM traffic per stream-collide launch from one ncu capture, keyed by dtype,
+# steps per launch and schedule, with the hash of the kernel code it was taken
+# on (null in the bench line once the code changes; comments do not count).
+# Captured at 8192^2 with 256-row segments (profiles/k_wave_8192_dram_traffic.md):
+# 33 strips of 256 slots and 32 segments, the same column-halo share (256/250
+# per output column) and segment length as the 16384^2 launch, so a launch's
+# traffic is 4x the capture's (nodes x4).  Mean of three launches.
 NCU_TRAFFIC = {
-    # four-step wavefront kernel: captured at 4096^2, where the segments are 32 rows long and
-    # neighbouring segments both read 6 of every 38 level-1 rows; at 16384^2 (128-row segments)
-    # that share is smaller, so the capture does not scale to the full launch: traffic stays null
-    # and the capture's figures are kept beside it
-    "f32_x4w": {"bytes_per_launch": None, "kernel_hash": "1a1de473db230565",
-                "ncu": {"case": "4096^2, 32-row segments", "dram_bytes_per_launch": 776.318976e6 + 491.771392e6,
-                        "dram_throughput_pct": 51.3, "issue_active_pct": 63.7, "top_stall": "long_scoreboard"}},
-    "f32_x3": {"bytes_per_launch": (673.150976e6 + 498.287616e6) * 16, "kernel_hash": "72ac5d7b008eb4b5",
-               "ncu": {"dram_throughput_pct": 58.9, "issue_active_pct": 62.9, "top_stall": "not_selected"}},
-    "f16s_x3": {"bytes_per_launch": (538.608128e6 + 366.969344e6) * 16, "kernel_hash": "72ac5d7b008eb4b5",
-                "ncu": {"dram_throughput_pct": 40.1, "issue_active_pct": 77.2, "top_stall": "not_selected"}},
-    "f32_x2": {"bytes_per_launch": (674.853888e6 + 493.407488e6) * 16, "kernel_hash": "357960238ea21163"},
-    "f32_x1": {"bytes_per_launch": (671.173632e6 + 485.997824e6) * 16, "kernel_hash": "357960238ea21163"},
-    "f16s_x1": {"bytes_per_launch": (536.988928e6 + 367.846144e6) * 16, "kernel_hash": "357960238ea21163"},
-    "f16s_x2": {"bytes_per_launch": (539.984384e6 + 364.976384e6) * 16, "kernel_hash": "357960238ea21163"},
+    "f32_x4w": {"bytes_per_launch": 4 * (2.76543e9 + 2.10507e9), "kernel_hash": "53f9735ba11b7673",
+                "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.76543e9,
+                        "dram_write_per_launch": 4 * 2.10507e9, "algorithmic_per_launch": 72 * 16384 ** 2}},
+    "f16s_x4w": {"bytes_per_launch": 4 * (2.21107e9 + 1.56953e9), "kernel_hash": "53f9735ba11b7673",
+                 "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.21107e9,
+                         "dram_write_per_launch": 4 * 1.56953e9, "algorithmic_per_launch": 56 * 16384 ** 2}},
 }
 
 
