@@ -253,9 +253,13 @@ int lbm_iterate_checked(lbm_ctx *ctx, int64_t n, int check_every, double *out);
 /* Iterate until the steady-state residual drops below tol (Sec. 2.1:
  * ||d u/dt|| < TOL "in some norm").  Reading used: every check_every (= k)
  * steps, r = max_x |u^n - u^(n-k)|_inf / (k max_x |u^n|_inf), accumulated in
- * FP64 (r = 0 when u = 0).  The first check after a reset only takes the
- * snapshot.  When tol is below the storage's rounding floor for k-step
- * windows (see lbm_batch_solve), the window is stretched to a multiple of k.  Stops when r < tol (LBM_OK), when a non-finite displacement
+ * FP64 (r = 0 when u = 0; for FP32 and FP16S storage u of the check step's
+ * input state is evaluated exactly as an FP32 pair).  The first check after a
+ * reset only takes the snapshot.  The window starts at a multiple of k long
+ * enough for the storage's estimated rounding floor and doubles (up to 64 k)
+ * after every check whose r is not below 0.95 of the previous one (see
+ * lbm_batch_solve), so a residual held up by rounding or decaying very slowly
+ * is measured over longer windows.  Stops when r < tol (LBM_OK), when a non-finite displacement
  * appears (LBM_ERR_DIVERGED) or after max_iters steps
  * (LBM_ERR_NOT_CONVERGED).  iters_out / residual_out (nullable) receive the
  * steps taken in this call and the last r.  Synchronous. */
@@ -354,12 +358,14 @@ typedef struct lbm_batch_report {
 /* Solve `count` problems to residual tol (checked every check_every >= 2
  * steps; a problem stops at the first check below tol, at divergence, or at
  * the first check at or beyond max_iters steps).  Rounding keeps a stored
- * state jittering by about J |u| (measured on converged states: J ~ 1.4e-7 to
- * 4.3e-7 for FP32; for FP16-shifted storage about 3e-4 / N, N = max(nx, ny)),
- * which floors a w-step residual near J / w; a problem whose tol is below that
- * for w = check_every is checked over windows of check_every * min(64, max(1,
- * ceil(2 J / (tol * check_every)))) steps instead, with J = 4e-7 (FP32) or
- * 6e-4 / N (FP16S).  dtype: LBM_F32 or LBM_F16S.
+ * state jittering by about J |u| (measured on converged states: J ~ 1.3e-7 to
+ * 4.3e-7 for FP32; 2.5e-7 to 1e-5 for FP16-shifted storage, larger for a
+ * shorter side and a larger nu), which floors a w-step residual near J / w.
+ * Each problem starts with windows of check_every * min(64, max(1, ceil(2 J /
+ * (tol * check_every)))) steps, J = 4e-7 (FP32) or 6e-4 / min(nx, ny) (FP16S),
+ * and its window doubles (up to 64 check_every) after every check whose
+ * residual is not below 0.95 of the previous one, as lbm_solve does.  dtype:
+ * LBM_F32 or LBM_F16S.
  * results[i] receives status, steps, residual and, where the pointers are
  * non-null, the FP64 displacement and stress (Table 2).  report may be null.
  * Synchronous.  Returns LBM_OK when every problem was run (per-problem

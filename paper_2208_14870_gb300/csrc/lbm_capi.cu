@@ -818,10 +818,13 @@ int lbm_solve(lbm_ctx* c, double tol, int64_t max_iters, int check_every, int64_
     if (!(tol >= 0.0) || max_iters < 0 || check_every < 1)
         return fail(LBM_ERR_ARG, "lbm_solve: bad tol, max_iters or check_every");
     if (max_iters > 0) c->state_zero = false;
-    // windows long enough that the storage's rounding jitter stays below tol
-    check_every *= check_period(c->dtype, tol, check_every, std::max(c->nx, c->ny));
+    // windows long enough that the storage's rounding jitter stays below tol,
+    // stretched while the residual stagnates (adapt_period)
+    const int k = check_every;
+    int period = check_period(c->dtype, tol, k, std::min(c->nx, c->ny));
+    check_every = k * period;
     int64_t done = 0;
-    double r = INFINITY;
+    double r = INFINITY, r_prev = INFINITY;
     int status = LBM_ERR_NOT_CONVERGED;
     while (done < max_iters) {
         const int64_t to_check = check_every - (c->step % check_every);
@@ -853,6 +856,9 @@ int lbm_solve(lbm_ctx* c, double tol, int64_t max_iters, int check_every, int64_
             status = LBM_OK;
             break;
         }
+        period = adapt_period(period, r, r_prev);
+        check_every = k * period;
+        r_prev = r;
     }
     if (iters_out) *iters_out = done;
     if (residual_out) *residual_out = r;

@@ -191,7 +191,9 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
     p.hexp = dtype_ == S_F16S ? f16s_exponent(gmax, nx, ny) : 0;
     p.tol = tol;
     p.max_iters = max_iters;
-    p.period = check_period(dtype_, tol, k_, std::max(nx, ny));
+    p.period = check_period(dtype_, tol, k_, std::min(nx, ny));
+    p.r_prev = INFINITY;
+    p.last_check = 0;
     p.state = P_RUNNING;
     probs_[slot] = p;
     ++nrunning_;
@@ -408,12 +410,17 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
         } else if (!p.snap_valid) {
             p.snap_valid = true;
             p.residual = INFINITY;
+            p.last_check = p.steps;
         } else {
-            const double window = (double)k_ * p.period;
+            const double window = (double)(p.steps - p.last_check);
+            p.last_check = p.steps;
             p.residual = raw[1] > 0.0 ? raw[0] / (window * raw[1]) : 0.0;
             if (p.residual < p.tol) {
                 p.status = LBM_OK;
                 done = true;
+            } else {
+                p.period = adapt_period(p.period, p.residual, p.r_prev);
+                p.r_prev = p.residual;
             }
         }
         if (!done && p.steps >= p.max_iters) {

@@ -30,7 +30,9 @@ struct HostProb {
     double tol = 0.0;
     bool snap_valid = false;
     bool check_now = false;    // the coming chunk checks this problem
-    int period = 1;            // residual window = period chunks
+    int period = 1;            // residual window = period chunks (adapt_period)
+    int64_t last_check = 0;    // steps at the previous check
+    double r_prev = 0.0;       // residual of the previous check
     int status = 0;            // lbm status when done
     double residual = 0.0;
     int64_t lups = 0;          // nodes x steps

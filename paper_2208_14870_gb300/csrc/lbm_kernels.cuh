@@ -1250,22 +1250,34 @@ inline int f16s_exponent(double gmax, int nx, int ny) {
     return e < -60 ? -60 : (e > 60 ? 60 : e);
 }
 
-// Residual windows per check interval k: rounding keeps a stored state
-// jittering by about J |u| (measured on converged states: J ~ 3e-15 for FP64,
-// 1.4e-7 .. 4.3e-7 for FP32, and for FP16-shifted storage about 3e-4 / N,
-// N = max(nx, ny), since its stored deviations are of size ~ u / N: 4e-6 at
-// N = 64, 8e-7 at 256, 2.5e-7 at 1024), which floors a w-step residual near
-// J / w; a problem asking for tol is therefore checked every
-// min(64, max(1, ceil(2 J / (tol k)))) intervals of k steps, with J = 4e-7
-// for FP32 and 6e-4 / N for FP16S (twice the measured values).  The cap
-// keeps divergence detection (made at checks) within 64 intervals; a tol
-// that would need more is below what the storage type can resolve.
-inline int check_period(int dtype, double tol, int k, int nmax) {
-    const double J = dtype == S_F16S ? 6e-4 / (double)(nmax > 1 ? nmax : 1)
+// Residual windows per check interval k: rounding keeps a converged stored
+// state jittering by about J |u|, which floors a w-step residual near J / w.
+// Measured (max|u^t - u^(t-w)| / max|u| long after convergence): FP64 ~3e-15;
+// FP32 1.3e-7 .. 4.3e-7 on every shape and nu tried; FP16-shifted storage
+// 2.5e-7 .. 1e-5, larger for a shorter lattice side (its stored deviations are
+// of size ~ |grad u| ~ u / min(nx, ny)) and for larger nu.  A solve asking for
+// tol starts with windows of min(64, max(1, ceil(2 J / (tol k)))) intervals of
+// k steps, J = 4e-7 (FP32) or 6e-4 / min(nx, ny) (FP16S), and adapt_period
+// stretches them while the residual stagnates, so a floor above the estimate
+// cannot stall the solve.  The cap keeps divergence detection (made at
+// checks) within 64 intervals; a tol that would need more is below what the
+// storage type can resolve.
+inline int check_period(int dtype, double tol, int k, int nmin) {
+    const double J = dtype == S_F16S ? 6e-4 / (double)(nmin > 1 ? nmin : 1)
                                      : (dtype == S_F32 ? 4e-7 : 3e-15);
     if (!(tol > 0.0) || k < 1) return 64;
     const double p = ceil(2.0 * J / (tol * (double)k));
     return p < 1.0 ? 1 : (p > 64.0 ? 64 : (int)p);
+}
+
+// The next window length (in intervals of k steps) after a check above tol:
+// doubled (up to 64) when the residual r did not fall below 0.95 of the
+// previous check's r_prev.  Decay faster than 5 % per window keeps the window;
+// a residual held up by the rounding floor J / w, or decaying very slowly, gets
+// longer windows (which lower the floor and cost fewer checks; the stopping
+// step moves by at most one window).
+inline int adapt_period(int period, double r, double r_prev) {
+    return (r > 0.95 * r_prev && period < 64) ? (period * 2 > 64 ? 64 : period * 2) : period;
 }
 
 inline int64_t step_tiles(int nx, int ny, int V) {

@@ -39,6 +39,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
 
+import paper_2208_14870_gb300 as P  # noqa: E402
 from paper_2208_14870_gb300 import Lattice  # noqa: E402
 
 
@@ -153,3 +154,37 @@ def test_f16s_residual_on_the_wavefront(k, windows):
     assert abs(got[0] - r_inf) <= 1e-12 * r_inf + tol, (got[0], r_inf)
     assert abs(got[1] - r_2) <= 1e-12 * r_2 + tol, (got[1], r_2)
     print("f16s wavefront k=%d: r_inf %.6e (device %.6e)" % (k, r_inf, got[0]))
+
+
+def _served_request(index):
+    """Request `index` of the seeded serving stream's requests with sides up to
+    2048 (the benchmark's served prefix)."""
+    reqs = [r for r in W.served_requests(rate_hz=20.0) if max(r.nx, r.ny) <= 2048]
+    return reqs[index]
+
+
+@pytest.mark.parametrize("index", [23, 74])
+def test_fp16s_windows_stretch_past_the_rounding_floor(index):
+    """Elongated FP16S requests of the serving stream (100 x 884, nu = 0.39;
+    1311 x 64, nu = 0.23): their rounding floor follows the shorter side, and a
+    window sized by the longer one never got below tol 1e-8.  With windows
+    sized by the shorter side and doubled while the residual stagnates,
+    lbm_solve and the batch arena both converge within a few times the steps
+    the slowest mode needs."""
+    import math
+    r = _served_request(index)
+    assert r.dtype == "f16s"
+    ks = [(int(a), int(b)) for a, b in zip(r.force.kx, r.force.ky)]
+    kk = min((2 * math.pi * kx / r.nx) ** 2 + (2 * math.pi * ky / r.ny) ** 2 for kx, ky in ks)
+    expect = math.log(r.mu * kk / 1e-8) / (r.mu * kk)
+    gx, gy = W.random_force_grid(r.force)
+    with Lattice(r.nx, r.ny, r.lam, r.mu, "f16s") as lat:
+        lat.set_force(gx, gy)
+        st, iters, res = lat.solve(1e-8, int(20 * expect), 100)
+    assert st == P.LBM_OK and res < 1e-8, (st, iters, res)
+    assert iters < 6 * expect, (iters, expect)
+    results, _ = P.batch_solve([(r.nx, r.ny, r.lam, r.mu, gx, gy)], dtype="f16s", tol=1e-8, check_every=100,
+                               max_iters=int(20 * expect), fields=False)
+    assert results[0]["status"] == P.LBM_OK and results[0]["iters"] < 6 * expect, results[0]
+    print("request %d %dx%d: lbm_solve %d steps, batch %d (slowest mode needs ~%.0f)" % (
+        index, r.nx, r.ny, iters, results[0]["iters"], expect))
