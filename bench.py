@@ -872,7 +872,7 @@ def main():
     ap.add_argument("--f64-iters", type=int, default=100,
                     help="pseudo-time steps per benchmark step of the FP64 variant")
     ap.add_argument("--variants", nargs="*",
-                    default=["f16s", "f32x3w", "f32x3", "f32x2", "f32x1", "f16sx3", "f16sx1", "f64"],
+                    default=["f16s", "f32x3", "f32x2", "f32x1", "f16sx1", "f64"],
                     help="extra storage variants; a suffix xK fixes K steps per launch on the tile "
                          "schedule, xKw on the wavefront schedule")
     ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")
