@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_arena_chunk2(const BatchArgs 
     }
 }
 
-// One wavefront item of a wide problem: strip and kArenaWaveSeg-row segment
-// `item`, the four steps of pass q (the buffers swap once per pass).
+// One wavefront item of a wide problem: strip and P.seg-row segment `item`,
+// the four steps of pass q (the buffers swap once per pass).
 template <int S, bool CHECK>
 __device__ __forceinline__ void arena_wave_item(const BatchArgs& A, const BatchProb& P, int item, int q,
                                                 float* sm, ResAcc<S>& acc) {
@@ -190,8 +190,8 @@ __device__ __forceinline__ void arena_wave_item(const BatchArgs& A, const BatchP
     c.qtheta = P.qtheta;
     c.theta = P.theta;
     const int nstrips = (P.nx + wv_ox<4>() - 1) / wv_ox<4>();
-    const int strip = item % nstrips, y0 = (item / nstrips) * kArenaWaveSeg;
-    wave_block<S, false, 4, CHECK, int>(a, c, sm, strip, y0, min(kArenaWaveSeg, P.ny - y0), acc);
+    const int strip = item % nstrips, y0 = (item / nstrips) * P.seg;
+    wave_block<S, false, 4, CHECK, int>(a, c, sm, strip, y0, min(P.seg, P.ny - y0), acc);
 }
 
 // The chunk of the wavefront schedule: nsteps / 4 passes of four steps.  In

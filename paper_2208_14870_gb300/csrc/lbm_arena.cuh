@@ -34,6 +34,7 @@ struct BatchProb {
     int64_t car_off;   // bytes into each carrier buffer (F16S)
     int64_t fs_off;    // bytes into the force/snapshot buffer
     int nx, ny, check, dtype, parity;   // check: this chunk's last step checks
+    int seg;                            // wavefront chunk: rows per wavefront item
     float q11, qs, qd, qtheta, theta, hscale, hinv;   // rates in the quarter form of collide
 };
 
@@ -108,20 +109,22 @@ private:
 constexpr int kTileTwoStep = 3;
 
 // Tile code of the wavefront chunk: problems from one strip width up advance
-// four steps per visit of a wavefront item (one strip, kArenaWaveSeg rows);
+// four steps per visit of a wavefront item (one strip by `seg` rows);
 // narrower ones take two two-step tiles per four steps (chunk length a
-// multiple of 4).
+// multiple of 4).  The segment length is chosen when the work list is built:
+// 256 rows, halved (down to 16) while the list would hold fewer than four
+// waves of resident blocks, so that a few large problems still fill the GPU.
 constexpr int kTileWave = 5;
-constexpr int kArenaWaveSeg = 64;
+constexpr int kArenaWaveSegMax = 256;
 
 // (wavefront items address a problem with 32-bit in-plane offsets)
 inline bool arena_wide(int nx, int ny) { return wave_fits(nx, ny) && (int64_t)nx * ny < (int64_t(1) << 31); }
 
-// Number of tiles of an nx x ny problem for tile code V.
-inline int64_t arena_tiles(int nx, int ny, int V) {
+// Number of tiles of an nx x ny problem for tile code V (seg: rows per
+// wavefront item of the wavefront chunk).
+inline int64_t arena_tiles(int nx, int ny, int V, int seg = kArenaWaveSegMax) {
     if (V == kTileWave)
-        return arena_wide(nx, ny) ? (int64_t)((nx + wv_ox<4>() - 1) / wv_ox<4>()) *
-                                        ((ny + kArenaWaveSeg - 1) / kArenaWaveSeg)
+        return arena_wide(nx, ny) ? (int64_t)((nx + wv_ox<4>() - 1) / wv_ox<4>()) * ((ny + seg - 1) / seg)
                                   : step2_tiles(nx, ny);
     return V == kTileTwoStep ? step2_tiles(nx, ny) : step_tiles(nx, ny, V);
 }

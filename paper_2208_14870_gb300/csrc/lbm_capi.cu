@@ -69,7 +69,8 @@ struct lbm_ctx {
     int64_t step = 0;
     bool snap_valid = false;
     int64_t snap_step = 0;
-    int hexp = 0;                  // F16S: stored deviation = deviation * 2^hexp
+    int hexp = 0;                  // F16S: the state is kept in units scaled by 2^hexp (store_f16s)
+    int force_exp = 0;             // F16S: the device force is scaled by 2^force_exp
     float hscale = 1.0f, hinv = 1.0f;
     double gmax = 0.0;             // max |g| of the current force
     bool state_zero = true;        // state is the zero state (create / reset)
@@ -363,19 +364,39 @@ void free_all(lbm_ctx* c) {
 // FP16-shifted storage: scale exponent from the force (f16s_exponent).
 int half_exponent(const lbm_ctx* c, double gmax) { return f16s_exponent(gmax, c->nx, c->ny); }
 
-// Switch the FP16 scale to 2^e, rescaling the stored deviations if asked.
+// Switch the FP16S scale to 2^e.  rescale: the state is non-zero and is
+// carried over -- stored deviations and carriers are multiplied by the power
+// of two (the residual snapshot, in the old units, is dropped).  The device
+// force always follows the scale (sync_force_scale).
+int sync_force_scale(lbm_ctx* c);
+
 int set_half_exponent(lbm_ctx* c, int e, bool rescale) {
-    if (e == c->hexp) return LBM_OK;
-    c->staged_fields = false;
-    if (rescale) {
-        const float factor = std::ldexp(1.0f, e - c->hexp);
-        k_rescale_half<<<1024, 256, 0, c->stream>>>(static_cast<__half*>(c->pop[c->cur]),
-                                                   8 * c->plane, factor);
-        CK(cudaGetLastError());
+    if (e != c->hexp) {
+        c->staged_fields = false;
+        if (rescale) {
+            const float factor = std::ldexp(1.0f, e - c->hexp);
+            k_rescale_half<<<1024, 256, 0, c->stream>>>(static_cast<__half*>(c->pop[c->cur]),
+                                                       8 * c->plane, factor);
+            CK(cudaGetLastError());
+            k_scale_float<<<1024, 256, 0, c->stream>>>(c->car[c->cur], 2 * c->plane, factor);
+            CK(cudaGetLastError());
+            c->snap_valid = false;
+        }
+        c->hexp = e;
+        c->hscale = std::ldexp(1.0f, e);
+        c->hinv = std::ldexp(1.0f, -e);
     }
-    c->hexp = e;
-    c->hscale = std::ldexp(1.0f, e);
-    c->hinv = std::ldexp(1.0f, -e);
+    return sync_force_scale(c);
+}
+
+// FP16S: bring the FP32 force on the device to the state's scale 2^hexp.
+int sync_force_scale(lbm_ctx* c) {
+    if (c->dtype != LBM_F16S || c->force_exp == c->hexp) return LBM_OK;
+    c->staged_fields = false;
+    k_scale_float<<<1024, 256, 0, c->stream>>>(static_cast<float*>(c->force), 2 * c->plane,
+                                               std::ldexp(1.0f, c->hexp - c->force_exp));
+    CK(cudaGetLastError());
+    c->force_exp = c->hexp;
     return LBM_OK;
 }
 
@@ -394,6 +415,7 @@ int set_force_dev(lbm_ctx* c, const double* gx, const double* gy) {
         k_force_ingest<float><<<2048, 256, 0, c->stream>>>(gx, gy, fx, fx + c->plane, c->n, c->absmax, c->bad);
     }
     CK(cudaGetLastError());
+    c->force_exp = 0;   // converted as given
     CK(cudaMemcpyAsync(c->pinned, c->absmax, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(c->pinned + 1, c->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost,
                        c->stream));
@@ -404,7 +426,8 @@ int set_force_dev(lbm_ctx* c, const double* gx, const double* gy) {
     std::memcpy(&bad, c->pinned + 1, sizeof(unsigned int));
     if (bad) return fail(LBM_ERR_ARG, "lbm_set_force: non-finite force");
     c->gmax = gmax;
-    if (c->dtype != LBM_F16S || gmax == 0.0) return LBM_OK;
+    if (c->dtype != LBM_F16S) return LBM_OK;
+    if (gmax == 0.0) return sync_force_scale(c);
     int e = half_exponent(c, gmax);
     // A non-zero state keeps its scale unless the new force asks for a
     // smaller one: growing the stored values could overflow FP16.
@@ -433,19 +456,22 @@ int read_residual(lbm_ctx* c, double out[kRes]) {
 }
 
 // Convert the raw reduction [max|du|, max|u|, sum du^2, sum u^2, bad] over a
-// window of `steps` steps into [r_inf, r_2, max|u|, ||u||_2, bad].
-void finish_residual(const double raw[kRes], int64_t steps, double out[kRes]) {
+// window of `steps` steps into [r_inf, r_2, max|u|, ||u||_2, bad]; `unscale`
+// takes the norms of u out of the state's scaled units (FP16S: 2^-hexp).
+void finish_residual(const double raw[kRes], int64_t steps, double out[kRes], double unscale) {
     const double k = double(steps > 0 ? steps : 1);
     out[0] = raw[1] > 0.0 ? raw[0] / (k * raw[1]) : 0.0;
     out[1] = raw[3] > 0.0 ? std::sqrt(raw[2]) / (k * std::sqrt(raw[3])) : 0.0;
-    out[2] = raw[1];
-    out[3] = std::sqrt(raw[3]);
+    out[2] = raw[1] * unscale;
+    out[3] = std::sqrt(raw[3]) * unscale;
     out[4] = raw[4];
     if (raw[4] != 0.0 || !std::isfinite(raw[0]) || !std::isfinite(raw[1])) {
         out[0] = out[1] = INFINITY;
         out[4] = 1.0;
     }
 }
+
+double norm_unscale(const lbm_ctx* c) { return c->dtype == LBM_F16S ? (double)c->hinv : 1.0; }
 
 }  // namespace
 
@@ -802,9 +828,9 @@ int lbm_iterate_checked(lbm_ctx* c, int64_t n, int check_every, double* out) {
         double raw[kRes];
         rc = read_residual(c, raw);
         if (rc) return rc;
-        if (any) finish_residual(raw, last_window, out);
+        if (any) finish_residual(raw, last_window, out, norm_unscale(c));
         else {
-            finish_residual(raw, 1, out);
+            finish_residual(raw, 1, out, norm_unscale(c));
             out[0] = out[1] = INFINITY;
         }
     }
@@ -844,7 +870,7 @@ int lbm_solve(lbm_ctx* c, double tol, int64_t max_iters, int check_every, int64_
         const int64_t window = c->step - c->snap_step;
         c->snap_valid = true;
         c->snap_step = c->step;
-        finish_residual(raw, window, res);
+        finish_residual(raw, window, res, norm_unscale(c));
         if (res[4] != 0.0) {
             status = LBM_ERR_DIVERGED;
             r = INFINITY;

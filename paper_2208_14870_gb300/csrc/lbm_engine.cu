@@ -171,6 +171,13 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
         h_force_[i] = (float)a;
         h_force_[n + i] = (float)b;
     }
+    p.hexp = dtype_ == S_F16S ? f16s_exponent(gmax, nx, ny) : 0;
+    if (p.hexp != 0) {
+        // FP16S keeps its state, the force included, in units scaled by 2^hexp
+        // (store_f16s); the power of two is exact
+        const float sc = std::ldexp(1.0f, p.hexp);
+        for (int64_t i = 0; i < 2 * n; ++i) h_force_[i] *= sc;
+    }
     ECK(cudaMemcpyAsync(fs_ + p.fs_off, h_force_, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, st_));
     ECK(cudaMemsetAsync(fs_ + p.fs_off + sizeof(float) * 2 * n, 0, sizeof(float2) * 2 * n, st_));
     ECK(cudaMemsetAsync(pop_[0] + p.pop_off, 0, p.pop_bytes, st_));
@@ -188,7 +195,6 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
     p.q11 = (float)(0.25 * (1.0 - 1.0 / (mu / theta + 0.5)));
     p.qs = (float)(0.25 * (1.0 - 1.0 / (2.0 * K / (1.0 + theta) + 0.5)));
     p.qd = (float)(0.25 * (1.0 - 1.0 / (2.0 * mu / (1.0 - theta) + 0.5)));
-    p.hexp = dtype_ == S_F16S ? f16s_exponent(gmax, nx, ny) : 0;
     p.tol = tol;
     p.max_iters = max_iters;
     p.period = check_period(dtype_, tol, k_, std::min(nx, ny));
@@ -202,10 +208,10 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
     return slot;
 }
 
-int64_t ArenaEngine::running_tiles(int V) const {
+int64_t ArenaEngine::running_tiles(int V, int seg) const {
     int64_t t = 0;
     for (const auto& p : probs_)
-        if (p.state == P_RUNNING) t += arena_tiles(p.nx, p.ny, V);
+        if (p.state == P_RUNNING) t += arena_tiles(p.nx, p.ny, V, seg);
     return t;
 }
 
@@ -230,7 +236,15 @@ int64_t ArenaEngine::free_nodes_hint() const {
 }
 
 int ArenaEngine::upload_tiles(int V, std::string* err) {
-    const int64_t nt = running_tiles(V);
+    if (V == kTileWave) {
+        // longest segments that still give four waves of resident blocks
+        const int64_t want = 4LL * grid_blocks(V);
+        int seg = kArenaWaveSegMax;
+        while (seg > 16 && running_tiles(V, seg) < want) seg /= 2;
+        if (seg != wave_seg_) desc_dirty_ = true;
+        wave_seg_ = seg;
+    }
+    const int64_t nt = running_tiles(V, wave_seg_);
     if (nt > (int64_t)INT32_MAX) {
         if (err) *err = "arena: too many tiles";
         return LBM_ERR_ARG;
@@ -265,7 +279,7 @@ int ArenaEngine::upload_tiles(int V, std::string* err) {
             const HostProb& p = probs_[s];
             if (p.state != P_RUNNING) continue;
             if (V == kTileWave && arena_wide(p.nx, p.ny) != (pass == 0)) continue;
-            const int64_t m = arena_tiles(p.nx, p.ny, V);
+            const int64_t m = arena_tiles(p.nx, p.ny, V, wave_seg_);
             for (int64_t i = 0; i < m; ++i) h_tiles_[t++] = make_uint2((unsigned)s, (unsigned)i);
         }
         if (pass == 0) nwide = t;
@@ -359,6 +373,7 @@ int ArenaEngine::run_chunk(int V, float* device_ms, std::string* err) {
             b.check = p.check_now ? 1 : 0;
             b.dtype = dtype_;
             b.parity = p.parity;
+            b.seg = wave_seg_;
             b.q11 = p.q11;
             b.qs = p.qs;
             b.qd = p.qd;

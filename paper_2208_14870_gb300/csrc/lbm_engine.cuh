@@ -66,7 +66,7 @@ public:
     void release(int slot);
     const HostProb& prob(int slot) const { return probs_[slot]; }
     int running() const { return nrunning_; }
-    int64_t running_tiles(int V) const;
+    int64_t running_tiles(int V, int seg = kArenaWaveSegMax) const;
     int64_t running_nodes() const;
     // Arena bytes held by admitted problems (running or finished, not released).
     int64_t resident_bytes() const;
@@ -103,6 +103,7 @@ private:
     uint2* h_tiles_ = nullptr;        // pinned
     int64_t h_tiles_cap_ = 0;
     int tiles_V_ = 0;                 // V the device tile list was built for
+    int wave_seg_ = kArenaWaveSegMax; // rows per wavefront item of the current list
     bool tiles_dirty_ = true;
     bool desc_dirty_ = true;
     float* h_force_ = nullptr;        // pinned FP32 staging

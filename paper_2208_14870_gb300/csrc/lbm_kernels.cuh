@@ -71,7 +71,7 @@ struct StepParams {
     float* cdst;
     const void* gx;         // force planes (G)
     const void* gy;
-    float hscale;           // F16S: stored = deviation * hscale (power of two)
+    float hscale;           // F16S: the state's scale 2^e (see store_f16s)
     float hinv;             // 1 / hscale
     void* snap;             // residual: u_x, u_y snapshot, 2 planes of nx*ny (ResSnap)
     double* partials;       // residual: kRes doubles per block
@@ -105,14 +105,18 @@ template <> struct ResAcc<S_F64> {
 };
 
 // max(m, |h + l|) on normalised pairs (|l| <= ulp(h) / 2), lexicographically.
+// Once a thread's running maximum is established few nodes reach it, so the
+// full comparison sits behind one test of the hi part.
 __device__ __forceinline__ void pair_max_abs(float& mh, float& ml, float h, float l) {
-    if (h < 0.0f) {
-        h = -h;
-        l = -l;
-    }
-    if (h > mh || (h == mh && l > ml)) {
-        mh = h;
-        ml = l;
+    if (fabsf(h) >= mh) {
+        if (h < 0.0f) {
+            h = -h;
+            l = -l;
+        }
+        if (h > mh || l > ml) {
+            mh = h;
+            ml = l;
+        }
     }
 }
 
@@ -258,23 +262,23 @@ __device__ __forceinline__ void pull_load(const StepParams& a, I r0, I rm, I rp,
 }
 
 // The pre-collision populations f_p(x) from the pulled stored values
-// (FP16S: deviation / scale + the equilibrium part of the source carrier).
+// (FP16S: the stored deviation + the equilibrium part of the source carrier,
+// both in the state's scaled units; see store_f16s).
 template <int S>
 __device__ __forceinline__ void pull_decode(const StepParams& a, const Pulled<S>& q,
                                             typename StoreT<S>::T f[8], typename StoreT<S>::T theta) {
     using T = typename StoreT<S>::T;
     if constexpr (S == S_F16S) {
-        const float hinv = a.hinv;
+        (void)a;
         const float k1 = 0.5f * (1.0f - theta), k5 = 0.25f * theta;
-        // (the FP16 value times the power-of-two 1/scale is exact)
-        f[0] = fmad(k1, q.c[0].x, __half2float(q.p[0]) * hinv);
-        f[1] = fmad(k1, q.c[1].y, __half2float(q.p[1]) * hinv);
-        f[2] = fmad(-k1, q.c[2].x, __half2float(q.p[2]) * hinv);
-        f[3] = fmad(-k1, q.c[3].y, __half2float(q.p[3]) * hinv);
-        f[4] = fmad(k5, q.c[4].x + q.c[4].y, __half2float(q.p[4]) * hinv);
-        f[5] = fmad(k5, q.c[5].y - q.c[5].x, __half2float(q.p[5]) * hinv);
-        f[6] = fmad(-k5, q.c[6].x + q.c[6].y, __half2float(q.p[6]) * hinv);
-        f[7] = fmad(k5, q.c[7].x - q.c[7].y, __half2float(q.p[7]) * hinv);
+        f[0] = fmad(k1, q.c[0].x, __half2float(q.p[0]));
+        f[1] = fmad(k1, q.c[1].y, __half2float(q.p[1]));
+        f[2] = fmad(-k1, q.c[2].x, __half2float(q.p[2]));
+        f[3] = fmad(-k1, q.c[3].y, __half2float(q.p[3]));
+        f[4] = fmad(k5, q.c[4].x + q.c[4].y, __half2float(q.p[4]));
+        f[5] = fmad(k5, q.c[5].y - q.c[5].x, __half2float(q.p[5]));
+        f[6] = fmad(-k5, q.c[6].x + q.c[6].y, __half2float(q.p[6]));
+        f[7] = fmad(k5, q.c[7].x - q.c[7].y, __half2float(q.p[7]));
     } else {
         (void)a;
         (void)theta;
@@ -293,23 +297,30 @@ __device__ __forceinline__ void gather(const StepParams& a, int64_t r0, int64_t 
     pull_decode<S>(a, q, f, theta);
 }
 
-// FP16-shifted store of one node: the deviations N (unscaled, FP32) are
-// rounded to FP16, and the FP32 carriers absorb the first moments of the
-// ROUNDED deviations, c10 = m*_10 - m_10(N_rounded), so that the stored state
+// FP16-shifted store of one node: the deviations N (FP32) are rounded to
+// FP16, and the FP32 carriers absorb the first moments of the ROUNDED
+// deviations, c10 = m*_10 - m_10(N_rounded), so that the stored state
 // N_rounded + E(c) keeps the first moments m*_10, m*_01 exactly (E(c) has
 // first moments c, no second moments).  Without this, the rounding of N would
 // feed the conserved mean-displacement mode every step and u would drift.
+// Scaled units: an FP16S lattice keeps its whole FP32 state -- carriers,
+// force, intermediate populations, residual snapshot -- multiplied by its
+// power-of-two scale 2^e (StepParams::hscale), chosen so that the deviations
+// sit well inside FP16's normal range.  The scale commutes with every
+// rounding, so this is the same arithmetic as unscaled values with the FP16
+// rounding done on N 2^e, without a multiplication per population in the
+// decode and two here; only the recovery, the export, the import and the
+// reported norms of u convert.
 __device__ __forceinline__ void store_f16s(const StepParams& a, int64_t idx, const float n[8],
                                            float m10s, float m01s) {
     __half* d = static_cast<__half*>(a.dst);
     const int64_t pl = a.plane;
-    const float hs = a.hscale, hi = a.hinv;
     float r[8];
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
-        const __half h = __float2half_rn(n[p] * hs);
+        const __half h = __float2half_rn(n[p]);
         d[p * pl + idx] = h;
-        r[p] = __half2float(h) * hi;
+        r[p] = __half2float(h);
     }
     const float e10 = (r[0] - r[2]) + ((r[4] - r[6]) - (r[5] - r[7]));
     const float e01 = (r[1] - r[3]) + ((r[4] - r[6]) + (r[5] - r[7]));
@@ -1118,12 +1129,14 @@ k_fields(const StepParams a, const Coef<double> c, typename StoreT<S>::T theta, 
         md = (double)hd + (double)__fadd_rn(ed, __fsub_rn(e13, e24));
         ms = (double)hs + (double)__fadd_rn(__fadd_rn(es, __fadd_rn(et, __fadd_rn(e13, e24))), 2.0f * l22);
     }
+    // (FP16S: back from the state's scaled units, a power of two)
+    const double un = S == S_F16S ? (double)a.hinv : 1.0;
     const double mb11 = c.b11 * m11, mbs = c.bs * ms, mbd = c.bd * md;
-    if (out.p[0]) out.p[0][idx] = u;
-    if (out.p[1]) out.p[1][idx] = v;
-    if (out.p[2]) out.p[2][idx] = -0.5 * (mbs + mbd);
-    if (out.p[3]) out.p[3][idx] = -0.5 * (mbs - mbd);
-    if (out.p[4]) out.p[4][idx] = -mb11;
+    if (out.p[0]) out.p[0][idx] = u * un;
+    if (out.p[1]) out.p[1][idx] = v * un;
+    if (out.p[2]) out.p[2][idx] = -0.5 * (mbs + mbd) * un;
+    if (out.p[3]) out.p[3][idx] = -0.5 * (mbs - mbd) * un;
+    if (out.p[4]) out.p[4][idx] = -mb11 * un;
 }
 
 // Pre-collision populations of the current state into 8 FP64 planes.
@@ -1140,8 +1153,10 @@ k_export(const StepParams a, typename StoreT<S>::T theta, double* out) {
     T f[8];
     gather<S>(a, r0, rm, rp, x, wrap_dec(x, nx), wrap_inc(x, nx), f, theta);
     const int64_t idx = r0 + x, n = (int64_t)nx * ny;
+    // (FP16S: back from the state's scaled units; a power of two, exact)
+    const double unscale = S == S_F16S ? (double)a.hinv : 1.0;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) out[p * n + idx] = double(f[p]);
+    for (int p = 0; p < 8; ++p) out[p * n + idx] = double(f[p]) * unscale;
 }
 
 // Load pre-collision populations f (8 FP64 planes): the stored post-collision
@@ -1159,16 +1174,18 @@ k_import(const StepParams a, typename StoreT<S>::T theta, const double* in) {
     const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
     const int64_t n = (int64_t)nx * ny;
     const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
-    // f*_p(x) = f_p(x + c_p)
+    // f*_p(x) = f_p(x + c_p); FP16S: in the state's scaled units (the power
+    // of two commutes with the rounding to FP32)
+    const T sc = S == S_F16S ? T(a.hscale) : T(1);
     T fs[8];
-    fs[0] = T(in[0 * n + r0 + xp]);
-    fs[1] = T(in[1 * n + rp + x]);
-    fs[2] = T(in[2 * n + r0 + xm]);
-    fs[3] = T(in[3 * n + rm + x]);
-    fs[4] = T(in[4 * n + rp + xp]);
-    fs[5] = T(in[5 * n + rp + xm]);
-    fs[6] = T(in[6 * n + rm + xm]);
-    fs[7] = T(in[7 * n + rm + xp]);
+    fs[0] = T(in[0 * n + r0 + xp]) * sc;
+    fs[1] = T(in[1 * n + rp + x]) * sc;
+    fs[2] = T(in[2 * n + r0 + xm]) * sc;
+    fs[3] = T(in[3 * n + rm + x]) * sc;
+    fs[4] = T(in[4 * n + rp + xp]) * sc;
+    fs[5] = T(in[5 * n + rp + xm]) * sc;
+    fs[6] = T(in[6 * n + rm + xm]) * sc;
+    fs[7] = T(in[7 * n + rm + xp]) * sc;
     const int64_t idx = r0 + x;
     P* d = static_cast<P*>(a.dst);
     if constexpr (S == S_F16S) {
@@ -1214,6 +1231,9 @@ __global__ void k_force_ingest(const double* gx, const double* gy, G* ox, G* oy,
 
 // F16S: multiply every stored deviation by `factor` (a power of two).
 __global__ void k_rescale_half(__half* h, int64_t count, float factor);
+// Multiply `count` floats by `factor` (a power of two: exact unless the result
+// leaves FP32's normal range).
+__global__ void k_scale_float(float* v, int64_t count, float factor);
 
 // Grid-level pass of the residual when the check launch wrote per-block
 // partials only (StepParams::counter == nullptr): one block combines the

@@ -3,6 +3,12 @@
 
 namespace lbm {
 
+__global__ void k_scale_float(float* v, int64_t count, float factor) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] *= factor;
+}
+
 __global__ void k_rescale_half(__half* h, int64_t count, float factor) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
