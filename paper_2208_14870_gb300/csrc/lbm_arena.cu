@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kWvW, 2) k_arena_wave(const BatchArgs A) {
 
 template <int S>
 static cudaError_t wave_arena_allow_smem() {
-    return cudaFuncSetAttribute(k_arena_wave<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, wv_smem<4>());
+    return cudaFuncSetAttribute(k_arena_wave<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, wv_smem<S, 4>());
 }
 
 template <int S>
@@ -262,7 +262,7 @@ static cudaError_t launch_wave_chunk(const BatchArgs& a, int grid, cudaStream_t 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kWvW);
-    cfg.dynamicSmemBytes = wv_smem<4>();
+    cfg.dynamicSmemBytes = wv_smem<S, 4>();
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -350,7 +350,7 @@ template <int S>
 static int occw() {
     if (wave_arena_allow_smem<S>() != cudaSuccess) return 0;
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_arena_wave<S>, kWvW, wv_smem<4>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_arena_wave<S>, kWvW, wv_smem<S, 4>());
     return b;
 }
 

@@ -190,7 +190,9 @@ cudaError_t launch_step3(lbm_ctx* c) {
 // waves of resident blocks (short segments cost 2(T - j) extra rows at level j).
 int wave_seg(const lbm_ctx* c, int T) {
     if (c->wave > 0) return c->wave;
-    const int64_t want = 4LL * (c->nsm > 0 ? c->nsm : 1) * (T == 3 ? wv_minb<3>() : wv_minb<4>());
+    const int minb = c->dtype == LBM_F16S ? (T == 3 ? wv_minb<S_F16S, 3>() : wv_minb<S_F16S, 4>())
+                                          : (T == 3 ? wv_minb<S_F32, 3>() : wv_minb<S_F32, 4>());
+    const int64_t want = 4LL * (c->nsm > 0 ? c->nsm : 1) * minb;
     int seg = kWvSegDefault;
     while (seg > 16 && (T == 3 ? wave_blocks<3>(c->nx, c->ny, seg) : wave_blocks<4>(c->nx, c->ny, seg)) < want)
         seg /= 2;

@@ -81,12 +81,19 @@ __device__ __forceinline__ Mom<T> moments(const T f[8]) {
 // 4 is a power of two, (c/4) * m rounds to exactly (c * m)/4: the stored
 // populations are the same bits as without it, at six fewer multiplications
 // per node.
+// The displacement u = mbar_10, v = mbar_01 of raw moments m (Eqs. coll10,
+// coll01; Table 2).
+template <typename T>
+__device__ __forceinline__ void displacement(const Mom<T>& m, T gx, T gy, T& u, T& v) {
+    u = m.m10 + T(0.5) * gx;
+    v = m.m01 + T(0.5) * gy;
+}
+
 template <typename T, bool GEN>
 __device__ __forceinline__ Mom<T> collide(const Mom<T>& m, T gx, T gy, const Coef<T>& c,
                                           T& u, T& v) {
     Mom<T> s;
-    u = m.m10 + T(0.5) * gx;
-    v = m.m01 + T(0.5) * gy;
+    displacement(m, gx, gy, u, v);
     s.m10 = m.m10 + gx;
     s.m01 = m.m01 + gy;
     s.m11 = rmul(c.q11, m.m11);
@@ -154,6 +161,16 @@ __device__ __forceinline__ void populations(const Mom<T>& s, T f[8]) {
     f[6] = h1 - h3;
     f[5] = h2 + h4;
     f[7] = h2 - h4;
+}
+
+// Post-collision populations straight from the raw moments: collide, then
+// populations (the standard rates drop m*_22).  (Merging the two into fused
+// multiply-adds on the raw moments saves two operations per node but measured
+// slower in the four-step wavefront kernel.)
+template <bool GEN, typename T>
+__device__ __forceinline__ void collide_populations(const Mom<T>& m, T gx, T gy, const Coef<T>& c, T& u, T& v,
+                                                    T f[8]) {
+    populations<!GEN>(collide<T, GEN>(m, gx, gy, c, u, v), f);
 }
 
 // Shifted FP16 storage.  The equilibrium-type part of a post-collision state

@@ -327,26 +327,54 @@ __device__ __forceinline__ void store_f16s(const StepParams& a, int64_t idx, con
     reinterpret_cast<float2*>(a.cdst)[idx] = make_float2(m10s - e10, m01s - e01);
 }
 
-// Store the post-collision state of node idx.
-// (s in the quarter form of collide; qtheta = theta / 4; GEN as for collide.)
+// The values a node stores after its collision (raw moments m, force g; GEN
+// as for collide): the eight post-collision populations, or for FP16S the
+// eight deviations N and the carriers (c10, c01) = (m*_10, m*_01); u, v
+// receive the displacement.  Computed apart from the stores so that kernels
+// can run it on every thread and predicate only the stores.
 template <int S, bool GEN>
-__device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
-                                              const Mom<typename StoreT<S>::T>& s,
-                                              typename StoreT<S>::T qtheta) {
+__device__ __forceinline__ void post_state(const Mom<typename StoreT<S>::T>& m, typename StoreT<S>::T gx,
+                                           typename StoreT<S>::T gy, const Coef<typename StoreT<S>::T>& c,
+                                           typename StoreT<S>::T& u, typename StoreT<S>::T& v,
+                                           typename StoreT<S>::T f[8], float& c10, float& c01) {
     using T = typename StoreT<S>::T;
-    using P = typename StoreT<S>::P;
-    P* d = static_cast<P*>(a.dst);
-    const int64_t pl = a.plane;
-    T f[8];
     if constexpr (S == S_F16S) {
-        populations<!GEN>(deviation_moments(s, qtheta), f);
-        store_f16s(a, idx, f, s.m10, s.m01);
+        const Mom<T> s = collide<T, GEN>(m, gx, gy, c, u, v);
+        populations<!GEN>(deviation_moments(s, c.qtheta), f);
+        c10 = s.m10;
+        c01 = s.m01;
     } else {
-        (void)qtheta;
-        populations<!GEN>(s, f);
+        collide_populations<GEN>(m, gx, gy, c, u, v, f);
+        c10 = c01 = 0.0f;
+    }
+}
+
+// Store the post_state values of node idx.
+template <int S>
+__device__ __forceinline__ void store_state(const StepParams& a, int64_t idx, const typename StoreT<S>::T f[8],
+                                            float c10, float c01) {
+    using P = typename StoreT<S>::P;
+    if constexpr (S == S_F16S) {
+        store_f16s(a, idx, f, c10, c01);
+    } else {
+        P* d = static_cast<P*>(a.dst);
+        const int64_t pl = a.plane;
 #pragma unroll
         for (int p = 0; p < 8; ++p) d[p * pl + idx] = P(f[p]);
     }
+}
+
+// Collide node idx (raw moments m, force g) and store its post-collision
+// state.
+template <int S, bool GEN>
+__device__ __forceinline__ void scatter_local(const StepParams& a, int64_t idx,
+                                              const Mom<typename StoreT<S>::T>& m,
+                                              typename StoreT<S>::T gx, typename StoreT<S>::T gy,
+                                              const Coef<typename StoreT<S>::T>& c) {
+    typename StoreT<S>::T f[8], u, v;
+    float c10, c01;
+    post_state<S, GEN>(m, gx, gy, c, u, v, f, c10, c01);
+    store_state<S>(a, idx, f, c10, c01);
 }
 
 // Residual reduction of a block.  Each thread's partials (ResAcc) are
@@ -488,10 +516,13 @@ __device__ __forceinline__ void step_tile(const StepParams& a,
         const int x = xb + 32 * j;
         if (x < nx) {
             const int64_t idx = r0 + x;
-            T u, v;
-            const Mom<T> s = collide<T, GEN>(moments(f[j]), gx[j], gy[j], c, u, v);
-            scatter_local<S, GEN>(a, idx, s, c.qtheta);
-            if (CHECK) check_node<S>(a, n, idx, acc, so[j], f[j], gx[j], gy[j], u, v);
+            const Mom<T> m = moments(f[j]);
+            scatter_local<S, GEN>(a, idx, m, gx[j], gy[j], c);
+            if (CHECK) {
+                T u, v;
+                displacement(m, gx[j], gy[j], u, v);
+                check_node<S>(a, n, idx, acc, so[j], f[j], gx[j], gy[j], u, v);
+            }
         }
     }
 }
@@ -615,7 +646,7 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 float u, v, fs[8];
-                populations<!GEN>(collide<float, GEN>(moments(f[b][j]), gx[k][j], gy[k][j], c, u, v), fs);
+                collide_populations<GEN>(moments(f[b][j]), gx[k][j], gy[k][j], c, u, v, fs);
 #pragma unroll
                 for (int p = 0; p < 8; ++p) s[p * PL + 32 * j] = fs[p];
             }
@@ -658,9 +689,13 @@ __device__ __forceinline__ void step2_tile(const StepParams& a, const Coef<float
             f[5] = s[5 * PL - kT2W + 1];
             f[6] = s[6 * PL + kT2W + 1];
             f[7] = s[7 * PL + kT2W - 1];
-            float u, v;
-            scatter_local<S, GEN>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
-            if (CHECK) check_node<S>(a, n, idx, acc, so[k][j], f, gx[k][j], gy[k][j], u, v);
+            const Mom<float> m = moments(f);
+            scatter_local<S, GEN>(a, idx, m, gx[k][j], gy[k][j], c);
+            if (CHECK) {
+                float u, v;
+                displacement(m, gx[k][j], gy[k][j], u, v);
+                check_node<S>(a, n, idx, acc, so[k][j], f, gx[k][j], gy[k][j], u, v);
+            }
         }
     }
 }
@@ -751,7 +786,7 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             float u, v, fs[8];
-            populations<!GEN>(collide<float, GEN>(moments(f[j]), gx[k][j], gy[k][j], c, u, v), fs);
+            collide_populations<GEN>(moments(f[j]), gx[k][j], gy[k][j], c, u, v, fs);
 #pragma unroll
             for (int p = 0; p < 8; ++p) s[p * PL + 32 * j] = fs[p];
         }
@@ -777,7 +812,7 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
             f[6] = s[6 * PL + kT3W + 1];
             f[7] = s[7 * PL + kT3W - 1];
             float u, v, fs[8];
-            populations<!GEN>(collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), fs);
+            collide_populations<GEN>(moments(f), gx[k][j], gy[k][j], c, u, v, fs);
             float* d = smB + r * kT3W + col;
 #pragma unroll
             for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
@@ -820,9 +855,13 @@ __device__ __forceinline__ void step3_tile(const StepParams& a, const Coef<float
             f[5] = s[5 * PL - kT3W + 1];
             f[6] = s[6 * PL + kT3W + 1];
             f[7] = s[7 * PL + kT3W - 1];
-            float u, v;
-            scatter_local<S, GEN>(a, idx, collide<float, GEN>(moments(f), gx[k][j], gy[k][j], c, u, v), c.qtheta);
-            if (CHECK) check_node<S>(a, n, idx, acc, so[k][j], f, gx[k][j], gy[k][j], u, v);
+            const Mom<float> m = moments(f);
+            scatter_local<S, GEN>(a, idx, m, gx[k][j], gy[k][j], c);
+            if (CHECK) {
+                float u, v;
+                displacement(m, gx[k][j], gy[k][j], u, v);
+                check_node<S>(a, n, idx, acc, so[k][j], f, gx[k][j], gy[k][j], u, v);
+            }
         }
     }
 }
@@ -861,17 +900,23 @@ k_step3(const StepParams a, const Coef<float> c) {
 // level tau per segment, and a level's ring holds four rows instead of a
 // whole tile, so four steps per launch fit.
 //
+// The vertical movers c_2 = (0, 1) and c_4 = (0, -1) are pulled from the
+// thread's own column, so they skip the rings: each level boundary keeps them
+// in a per-thread delay line (population 2 of the last three rows produced,
+// population 4 of the last one), and the rings hold the six other
+// populations.  Step 1 pulls into registers one row ahead of its use (FP32
+// with LBM_WV_LA2_F32: two rows) and loads the force two rows ahead (FP16S:
+// one row; its pulls carry the FP32 carriers too).
+//
 // Instruction economy (the kernel issues, it does not wait on HBM): the
 // iterations in which every level is active run in groups of four, so every
 // ring slot is a compile-time offset from one per-thread address and no
 // level tests whether it is active; only the first 3(T-1) and the last few
-// iterations of a segment take the general path.  Latency: the force of a
-// thread's column for the last 2(T-1)+1 rows stays in registers (step tau
-// uses the row step 1 loaded 2(tau-1) iterations earlier), and step 1 issues
-// the loads of its next row before the shared-memory work of the current
-// iteration, so no level waits on a global load it has just issued.  With
-// I = int (lattices below 2^31 nodes) global addresses are a 32-bit in-plane
-// offset on a per-plane base.
+// iterations of a segment take the general path.  The force of a thread's
+// column for the last 2(T-1)+1 rows stays in registers (step tau uses the row
+// step 1 loaded 2(tau-1) iterations earlier).  With I = int (lattices below
+// 2^31 nodes) global addresses are a 32-bit in-plane offset on a per-plane
+// base.
 //
 // CHECK: step T is the residual-check step (its input state is u^(t+T-1));
 // its snapshot loads run one iteration ahead, and the block's partials go to
@@ -883,43 +928,44 @@ k_step3(const StepParams a, const Coef<float> c) {
 #ifndef LBM_WV_NW
 #define LBM_WV_NW 8
 #endif
-// level-1 look-ahead per storage type: two rows ahead (1) or one (0); the
-// defaults are the faster of the two at 16384^2 on GB300 (FP32 3.63 against
-// 3.71 ms per four-step launch, FP16S 4.01 against 4.08 ms with one row)
-#ifndef LBM_WV_PREF2_F32
-#define LBM_WV_PREF2_F32 1
-#endif
-#ifndef LBM_WV_PREF2_F16S
-#define LBM_WV_PREF2_F16S 0
+// FP32 step 1: populations loaded two rows ahead (1) or one (0)
+#ifndef LBM_WV_LA2_F32
+#define LBM_WV_LA2_F32 1
 #endif
 constexpr int kWvNW = LBM_WV_NW;                 // warps per block
 constexpr int kWvW = 32 * kWvNW;                 // strip width (slot columns)
 constexpr int kWvRow = kWvW + 2;                 // ring row: the strip plus one pad column per side
 constexpr int kWvD = 4;                          // ring rows per level
+constexpr int kWvRP = 6;                         // populations held in a ring (all but 2 and 4)
 constexpr int kWvSegDefault = 256;               // output rows per block segment (default)
 template <int S>
-__host__ __device__ constexpr bool wv_pref2() { return S == S_F16S ? LBM_WV_PREF2_F16S != 0 : LBM_WV_PREF2_F32 != 0; }
+__host__ __device__ constexpr bool wv_la2() { return S == S_F32 && LBM_WV_LA2_F32 != 0; }
 static_assert(kWvW <= kThreads, "residual_reduce sizes its scratch by kThreads");
 template <int T> __host__ __device__ constexpr int wv_ox() { return kWvW - 2 * (T - 1); }
-template <int T> __host__ __device__ constexpr int wv_smem() { return (T - 1) * 8 * kWvD * kWvRow * (int)sizeof(float); }
-// resident blocks per SM the kernel is compiled for: 228 KB of shared memory
-// per SM, 1 KB reserved per block
-template <int T> constexpr int wv_minb() {
-    return (233472 / (wv_smem<T>() + 1024)) < (2048 / kWvW) ? (233472 / (wv_smem<T>() + 1024))
-                                                             : (2048 / kWvW);
+template <int S, int T> __host__ __device__ constexpr int wv_smem() {
+    return (T - 1) * kWvRP * kWvD * kWvRow * (int)sizeof(float);
+}
+// resident blocks per SM the kernel is compiled for: what 228 KB of shared
+// memory per SM allows (1 KB reserved per block), at most LBM_WV_MINB (the
+// register budget: 128 registers a thread at two blocks of 256 threads)
+#ifndef LBM_WV_MINB
+#define LBM_WV_MINB 2
+#endif
+template <int S, int T> constexpr int wv_minb() {
+    return (233472 / (wv_smem<S, T>() + 1024)) < LBM_WV_MINB ? (233472 / (wv_smem<S, T>() + 1024))
+                                                             : LBM_WV_MINB;
 }
 
 // One block's share of a wavefront launch: strip `strip`, output rows y0 ..
-// y0 + rows - 1, T steps; wv_ring is the block's (T-1) rings.  With CHECK the
-// thread's residual partials of level T are accumulated into acc.  Called by
-// k_wave (one block per strip and segment) and by the batched arena (one
-// call per work item).
+// y0 + rows - 1, T steps; wv_ring is the block's (T-1) rings.  With CHECK the thread's residual partials of
+// level T are accumulated into acc.  Called by k_wave (one block per strip
+// and segment) and by the batched arena (one call per work item).
 template <int S, bool GEN, int T, bool CHECK, typename I>
 __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float>& c, float* wv_ring,
                                            int strip, int y0, int rows, ResAcc<S>& acc) {
     static_assert(T >= 2 && T <= 4, "two to four steps per launch");
-    constexpr int W = kWvW, R = kWvRow, OX = wv_ox<T>(), PL = kWvD * kWvRow, RP = 8 * PL, D = kWvD - 1;
-    constexpr bool kWvPref2 = wv_pref2<S>();
+    constexpr int W = kWvW, R = kWvRow, OX = wv_ox<T>(), PL = kWvD * kWvRow, RP = kWvRP * PL, D = kWvD - 1;
+    constexpr bool PA2 = wv_la2<S>();             // populations two rows ahead
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
     const int xs = strip * OX - (T - 1) + t;      // lattice column of slot t (unwrapped)
@@ -941,22 +987,42 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     float hx[NH], hy[NH];
 #pragma unroll
     for (int k = 0; k < NH; ++k) hx[k] = hy[k] = 0.0f;
-    // Level 1 reads global memory two rows ahead (FP16S, whose pulls hold
-    // three times the registers: one), so its loads are in flight while the
-    // iterations before work from shared memory.  The row offsets of the next row to load advance one row per
-    // load (rows are loaded in order), with the periodic wrap.
-    Pulled<S> q[kWvPref2 ? 2 : 1];
-    float qg[kWvPref2 ? 2 : 1][2];
-    int ly = wrap_slot<false>(ybeg, ny);          // lattice row of the next load
+    // Delay lines of the vertical movers at the T - 1 level boundaries: v2[r][k]
+    // is population 2 (index 1) of the row ring r's producer made k + 1
+    // productions ago, v4[r] population 4 (index 3) of its last row.  The
+    // consumer (level r + 2) of local row j reads population 2 of row j - 1
+    // (made three iterations earlier) and population 4 of row j + 1 (one
+    // iteration earlier) before the producer (level r + 1) of the same
+    // iteration shifts the line; producers run in consecutive iterations, from
+    // three iterations before their consumer's first to one before its last.
+    float v2[T - 1][3], v4[T - 1];
+#pragma unroll
+    for (int r = 0; r < T - 1; ++r) v2[r][0] = v2[r][1] = v2[r][2] = v4[r] = 0.0f;
+    // Step 1's pulls (one row ahead, PA2: two) and the force (LA2: two rows
+    // ahead, else one) in registers.  The row offsets of the next row to load
+    // advance one row per load (rows are loaded in order), with the periodic
+    // wrap.
+    constexpr bool LA2 = S == S_F32;
+    Pulled<S> q[PA2 ? 2 : 1];
+    float qg[LA2 ? 2 : 1][2];
+    int ly = wrap_slot<false>(ybeg, ny);          // lattice row of the next population load
     I lr0 = (I)ly * nx, lrm = (I)wrap_dec(ly, ny) * nx, lrp = (I)wrap_inc(ly, ny) * nx;
-    auto load1 = [&](int b) {
-        pull_load<S, I>(a, lr0, lrm, lrp, x, xm, xp, q[b]);
-        qg[b][0] = ldg(gxp + lr0 + x);
-        qg[b][1] = ldg(gyp + lr0 + x);
+    int gly = ly;                                 // lattice row of the next force load
+    auto advance = [&]() {
         ly = wrap_inc(ly, ny);
         lrm = lr0;
         lr0 = lrp;
         lrp = (I)wrap_inc(ly, ny) * nx;
+    };
+    auto load_force = [&](int b) {
+        const I g = (I)gly * nx + x;
+        qg[b][0] = ldg(gxp + g);
+        qg[b][1] = ldg(gyp + g);
+        gly = wrap_inc(gly, ny);
+    };
+    auto load1 = [&](int b) {
+        pull_load<S, I>(a, lr0, lrm, lrp, x, xm, xp, q[b]);
+        advance();
     };
     // Residual check on level T: its snapshot entry is loaded one iteration ahead.
     ResSnap<S> so;
@@ -965,13 +1031,13 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     };
 
     // One iteration; FULL: every level active (ring slots fold to constants
-    // when i is a compile-time offset from a multiple of four).  Halo threads
-    // of a level compute values no valid slot reads (their pulls stay inside
-    // the padded ring rows), so no level branches per thread; only the
-    // stores of level T are predicated.
+    // when i is a compile-time offset from a multiple of four).
+    // Halo threads of a level compute values no valid slot reads (their pulls
+    // stay inside the padded ring rows), so no level branches per thread; only
+    // the stores of level T are predicated.
     auto iter = [&](int i, auto full_c, auto buf_c) {
         constexpr bool FULL = decltype(full_c)::value;
-        constexpr int b = decltype(buf_c)::value;   // load buffer of local row i (i mod 2 with
+        constexpr int b = decltype(buf_c)::value;   // load buffers of local row i (i mod 2 with
                                                     // two rows ahead, else 0)
         const bool l1 = FULL || i < n1;
 #pragma unroll
@@ -983,9 +1049,10 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
         hy[0] = qg[b][1];
         float f1[8];
         if (l1) {
-            pull_decode<S>(a, q[b], f1, c.theta);
-            const int next = kWvPref2 ? i + 2 : i + 1;
-            if (FULL || next < n1) load1(b);
+            constexpr int bq = PA2 ? b : 0;
+            pull_decode<S>(a, q[bq], f1, c.theta);
+            if (FULL || i + (PA2 ? 2 : 1) < n1) load1(bq);
+            if (FULL || i + (LA2 ? 2 : 1) < n1) load_force(b);
         }
         // Levels T..2: local row j = i - 2(tau - 1), pulled from ring tau - 1.
 #pragma unroll
@@ -997,52 +1064,74 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
             const int rm = ((j - 1) & D) * R, r0 = (j & D) * R, rp = ((j + 1) & D) * R;
             float f[8];
             f[0] = sp[0 * PL + r0 - 1];          // f_p(x) = f*_p(x - c_p)
-            f[1] = sp[1 * PL + rm];
-            f[2] = sp[2 * PL + r0 + 1];
-            f[3] = sp[3 * PL + rp];
-            f[4] = sp[4 * PL + rm - 1];
-            f[5] = sp[5 * PL + rm + 1];
-            f[6] = sp[6 * PL + rp + 1];
-            f[7] = sp[7 * PL + rp - 1];
-            float u, v;
+            f[1] = v2[tau - 2][2];
+            f[2] = sp[1 * PL + r0 + 1];
+            f[3] = v4[tau - 2];
+            f[4] = sp[2 * PL + rm - 1];
+            f[5] = sp[3 * PL + rm + 1];
+            f[6] = sp[4 * PL + rp + 1];
+            f[7] = sp[5 * PL + rp - 1];
             const float gx = hx[2 * (tau - 1)], gy = hy[2 * (tau - 1)];
-            const Mom<float> m = collide<float, GEN>(moments(f), gx, gy, c, u, v);
+            const Mom<float> m = moments(f);
             if (tau < T) {
-                float fs[8];
-                populations<!GEN>(m, fs);
+                float u, v, fs[8];
+                collide_populations<GEN>(m, gx, gy, c, u, v, fs);
                 float* d = rt + (tau - 1) * RP + r0;
-#pragma unroll
-                for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
-            } else if (store_ok) {
-                const I idx = (I)(ybeg + j) * nx + xs;   // row in [y0, y0 + rows), xs < nx
-                if (CHECK) {
-                    check_node<S>(a, n, (int64_t)idx, acc, so, f, gx, gy, u, v);
-                    if (FULL || i + 1 < iters) snap_next(i + 1);
+                d[0 * PL] = fs[0];
+                d[1 * PL] = fs[2];
+                d[2 * PL] = fs[4];
+                d[3 * PL] = fs[5];
+                d[4 * PL] = fs[6];
+                d[5 * PL] = fs[7];
+                v2[tau - 1][2] = v2[tau - 1][1];
+                v2[tau - 1][1] = v2[tau - 1][0];
+                v2[tau - 1][0] = fs[1];
+                v4[tau - 1] = fs[3];
+            } else {
+                // every thread collides; only the stores are predicated
+                float u, v, fs[8], c10, c01;
+                post_state<S, GEN>(m, gx, gy, c, u, v, fs, c10, c01);
+                if (store_ok) {
+                    const I idx = (I)(ybeg + j) * nx + xs;   // row in [y0, y0 + rows), xs < nx
+                    if (CHECK) {
+                        check_node<S>(a, n, (int64_t)idx, acc, so, f, gx, gy, u, v);
+                        if (FULL || i + 1 < iters) snap_next(i + 1);
+                    }
+                    store_state<S>(a, (int64_t)idx, fs, c10, c01);
                 }
-                scatter_local<S, GEN>(a, (int64_t)idx, m, c.qtheta);
             }
         }
         if (l1) {
             float u, v, fs[8];
-            populations<!GEN>(collide<float, GEN>(moments(f1), hx[0], hy[0], c, u, v), fs);
+            collide_populations<GEN>(moments(f1), hx[0], hy[0], c, u, v, fs);
             float* d = rt + (i & D) * R;
-#pragma unroll
-            for (int p = 0; p < 8; ++p) d[p * PL] = fs[p];
+            d[0 * PL] = fs[0];
+            d[1 * PL] = fs[2];
+            d[2 * PL] = fs[4];
+            d[3 * PL] = fs[5];
+            d[4 * PL] = fs[6];
+            d[5 * PL] = fs[7];
+            v2[0][2] = v2[0][1];
+            v2[0][1] = v2[0][0];
+            v2[0][0] = fs[1];
+            v4[0] = fs[3];
         }
         __syncthreads();
     };
 
     load1(0);
-    if (kWvPref2 && n1 > 1) load1(1);
+    if (PA2 && n1 > 1) load1(1);
+    load_force(0);
+    if (LA2 && n1 > 1) load_force(1);
     const int fb = 3 * (T - 1);                   // first iteration with every level active
     // last one whose level 1 still loads ahead
-    const int fe = rows + 2 * T - 3 - (kWvPref2 ? 2 : 1);
+    const int fe = n1 - 1 - (LA2 || PA2 ? 2 : 1);
     if (CHECK && store_ok) snap_next(fb);         // level T's first row is y0
     const int m0 = (fb + 3) >> 2, m1 = (fe + 1) >> 2;   // groups i = 4m .. 4m + 3 within [fb, fe]
     using B0 = std::integral_constant<int, 0>;
-    using B1 = std::integral_constant<int, kWvPref2 ? 1 : 0>;
+    using B1 = std::integral_constant<int, LA2 ? 1 : 0>;
     auto iter_any = [&](int i) {
-        if (kWvPref2 && (i & 1)) iter(i, std::false_type{}, B1{});
+        if (LA2 && (i & 1)) iter(i, std::false_type{}, B1{});
         else iter(i, std::false_type{}, B0{});
     };
     int i = 0;
@@ -1061,9 +1150,9 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
 }
 
 template <int S, bool GEN, int T, bool CHECK, typename I>
-__global__ void __launch_bounds__(kWvW, wv_minb<T>())
+__global__ void __launch_bounds__(kWvW, (wv_minb<S, T>()))
 k_wave(const StepParams a, const Coef<float> c, int seg) {
-    extern __shared__ float wv_ring[];            // (T-1) rings of 8 planes x kWvD rows x kWvRow
+    extern __shared__ float wv_ring[];            // (T-1) rings of 6 planes x kWvD rows x kWvRow, staging
     const int nstrips = (a.nx + wv_ox<T>() - 1) / wv_ox<T>();
     const int strip = (int)(blockIdx.x % (unsigned)nstrips);
     const int y0 = (int)(blockIdx.x / (unsigned)nstrips) * seg;

@@ -90,12 +90,12 @@ static cudaError_t launch_wave_k(const StepParams& a, const Coef<float>& c, int 
         std::lock_guard<std::mutex> lock(mu);
         if (!done[dev]) {
             e = cudaFuncSetAttribute(k_wave<S, GEN, T, CHECK, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     wv_smem<T>());
+                                     wv_smem<S, T>());
             if (e != cudaSuccess) return e;
             done[dev] = true;
         }
     }
-    k_wave<S, GEN, T, CHECK, I><<<grid, kWvW, wv_smem<T>(), st>>>(a, c, seg);
+    k_wave<S, GEN, T, CHECK, I><<<grid, kWvW, wv_smem<S, T>(), st>>>(a, c, seg);
     return cudaGetLastError();
 }
 

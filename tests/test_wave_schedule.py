@@ -1,12 +1,15 @@
 """Host check of the wavefront schedule of k_wave (no GPU): the kernel's level
 windows, its two-row lag between step levels, its four-row shared-memory
-rings and its register history of the force (level j reads the entry
-2(j - 1) rows back), replayed block by block in numpy on a toy per-node update with the
-same pull streaming, must give exactly T single steps -- every ring read
-finds the row it needs, every slot index stays inside its ring row, every
-output node is written once, and the periodic wrap of slot coordinates stays
-within one period.  The constants (ring depth, warps per block) are read from
-the kernel header so that the replay follows the compiled schedule."""
+rings of six populations, the per-thread delay lines that carry populations 2
+and 4 (the vertical movers, pulled from the thread's own column) across each
+level boundary, and its register history of the force (level j reads the
+entry 2(j - 1) rows back), replayed block by block in numpy on a toy per-node
+update with the same pull streaming, must give exactly T single steps -- every
+ring read finds the row it needs, every delay-line read the row it needs,
+every slot index stays inside its ring row, every output node is written
+once, and the periodic wrap of slot coordinates stays within one period.  The
+constants (ring depth, warps per block) are read from the kernel header so
+that the replay follows the compiled schedule."""
 import os
 import re
 
@@ -16,6 +19,7 @@ import pytest
 from conftest import ROOT
 
 C = [(1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+RING = [0, 2, 4, 5, 6, 7]          # populations held in the shared-memory rings
 
 
 def _constants():
@@ -65,6 +69,10 @@ def _wave(state, gx, gy, T, seg, W, D):
         held = np.full((T - 1, D), -10 ** 9)          # lattice row held by each ring slot
         ybeg = y0 - (T - 1)
         hist = [None] * (2 * (T - 1) + 1)              # force rows held in registers
+        nan_row = (None, np.full(W, np.nan))
+        v2 = [[nan_row] * 3 for _ in range(T - 1)]      # (row, values): last three productions
+        v4 = [nan_row] * (T - 1)                        # (row, values): last production
+        n1 = rows + 2 * (T - 1)
         for i in range(rows + 3 * (T - 1)):
             writes = []                                # applied after the block barrier
             reads = set()                              # ring slots read in this iteration
@@ -79,32 +87,50 @@ def _wave(state, gx, gy, T, seg, W, D):
                     assert held[tau - 2][(yl + dy) % D] == yl + dy
                     reads.add((tau - 2, (yl + dy) % D))
                 f = np.empty((8, int(act.sum())))
-                for p, (cx, cy) in enumerate(C):
+                for p in RING:
+                    cx, cy = C[p]
                     cols = t[act] - cx
                     assert cols.min() >= 0 and cols.max() < W
                     f[p] = ring[tau - 2][p][(yl - cy) % D][cols]
+                row, val = v2[tau - 2][2]              # population 2: c = (0, 1), from row yl - 1
+                assert row == yl - 1
+                f[1] = val[act]
+                row, val = v4[tau - 2]                 # population 4: c = (0, -1), from row yl + 1
+                assert row == yl + 1
+                f[3] = val[act]
                 assert not np.isnan(f).any()
                 yw = _wrap_slot(yl, ny)
                 g = _toy(f, gx[yw, x[act]], gy[yw, x[act]])
                 if tau < T:
                     writes.append((tau - 1, yl, act, g))
+                    # the delay lines shift as the producer runs (after this
+                    # iteration's consumer of the same boundary has read them)
+                    p2, p4 = np.full(W, np.nan), np.full(W, np.nan)
+                    p2[act], p4[act] = g[1], g[3]
+                    v2[tau - 1] = [(yl, p2)] + v2[tau - 1][:2]
+                    v4[tau - 1] = (yl, p4)
                 else:
                     assert 0 <= yl < ny and (xs[act] == x[act]).all()
                     out[:, yl, x[act]] = g
                     written[yl, x[act]] += 1
-            if i < rows + 2 * (T - 1):
+            if i < n1:
                 y1 = ybeg + i
                 y = _wrap_slot(y1, ny)
                 f = np.empty((8, W))
                 for p, (cx, cy) in enumerate(C):
                     f[p] = state[p][(y - cy) % ny][(x - cx) % nx]
-                writes.append((0, y1, np.ones(W, bool), _toy(f, gx[y, x], gy[y, x])))
+                g = _toy(f, gx[y, x], gy[y, x])
+                writes.append((0, y1, np.ones(W, bool), g))
+                v2[0] = [(y1, g[1])] + v2[0][:2]
+                v4[0] = (y1, g[3])
             # threads of one iteration are not ordered: no slot may be both
             # read and written between two barriers
             assert not reads & {(lv, yl % D) for lv, yl, _, _ in writes}
             for lv, yl, act, g in writes:
                 ring[lv][:, yl % D, :] = np.nan
-                ring[lv][:, yl % D, act] = g
+                held_vals = np.full((len(RING), W), np.nan)
+                held_vals[:, act] = g[RING]
+                ring[lv][RING, yl % D, :] = held_vals
                 held[lv][yl % D] = yl
     assert (written == 1).all()
     return out
