@@ -597,20 +597,32 @@ def run_ours(args, ws, rank, local):
 def run_e2e(args, gx, gy, torch, P, ws, dist):
     """Through the public API with host buffers: upload the force from pinned
     host memory, reset, iterate with residual checks, read displacement and
-    stress back into pinned host memory -- every step."""
+    stress back into pinned host memory -- every step.  With a pipeline of
+    p > 1, p lattices on their own streams are driven by p host threads (step
+    s on lattice s mod p) with copy-engine transfers (LBM_HOST_COPY), so one
+    lattice's transfers overlap another's steps; every step still carries its
+    own host-to-device and device-to-host copies."""
+    import threading
     n = args.n
+    pipe = max(1, args.e2e_pipeline)
     lam, mu = W.lame_2d(1.0, args.nu)
-    lat = P.Lattice(n, n, lam, mu, args.dtype)
     hgx = torch.from_numpy(gx).pin_memory()
     hgy = torch.from_numpy(gy).pin_memory()
-    outs = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(5)]
-    res = np.zeros(5)
+    lanes = []
+    for k in range(pipe):
+        lat = P.Lattice(n, n, lam, mu, args.dtype)
+        stream = None
+        if pipe > 1:
+            stream = torch.cuda.Stream()
+            lat.set_stream(stream.cuda_stream)
+            lat.host_transfer = P.LBM_HOST_COPY if args.e2e_transfer == "copy" else P.LBM_HOST_DIRECT
+        outs = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(5)]
+        lanes.append({"lat": lat, "stream": stream, "outs": outs, "res": np.zeros(5), "parts": np.zeros(4)})
 
-    parts = np.zeros(4)
-
-    def step():
+    def step(lane):
         # every call returns after its work is done (the library synchronises
         # its stream), so the host clock between calls splits the step
+        lat, outs, res = lane["lat"], lane["outs"], lane["res"]
         t = [time.perf_counter()]
         P.lbm_set_force(lat.ctx, hgx.data_ptr(), hgy.data_ptr())
         t.append(time.perf_counter())
@@ -621,31 +633,57 @@ def run_e2e(args, gx, gy, torch, P, ws, dist):
         t.append(time.perf_counter())
         P.lbm_get_stress(lat.ctx, outs[2].data_ptr(), outs[3].data_ptr(), outs[4].data_ptr())
         t.append(time.perf_counter())
-        parts[:] += np.diff(t)
+        lane["parts"][:] += np.diff(t)
 
-    for _ in range(args.e2e_warmup):
-        step()
+    def run(nsteps):
+        errors = []
+
+        def lane_loop(k):
+            try:
+                for _ in range(k, nsteps, pipe):
+                    step(lanes[k])
+            except Exception as e:  # re-raised on the main thread
+                errors.append(e)
+
+        threads = [threading.Thread(target=lane_loop, args=(k,)) for k in range(pipe)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errors:
+            raise errors[0]
+
+    run(args.e2e_warmup * pipe)
     torch.cuda.synchronize()
-    parts[:] = 0.0
+    for lane in lanes:
+        lane["parts"][:] = 0.0
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        step()
+    run(args.e2e_steps)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     t = torch.tensor([dt], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dt = float(t.item())
-    lat.close()
+    parts = sum(lane["parts"] for lane in lanes) / args.e2e_steps
+    for lane in lanes:
+        lane["lat"].close()
+    api = ("lbm_set_force(host) + lbm_reset + lbm_iterate_checked + "
+           "lbm_get_displacement/lbm_get_stress(host)")
+    if pipe > 1:
+        api += ", %d lattices on their own streams, one host thread each, %s" % (
+            pipe, "LBM_HOST_COPY (copy-engine transfers)" if args.e2e_transfer == "copy"
+            else "LBM_HOST_DIRECT (kernels read and write the pinned host arrays)")
     return {"value": float(n) * n * args.iters * args.e2e_steps * ws / dt / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 5 * n * n * 8 + 5 * 8,
-            "steps": args.e2e_steps, "ms_per_step": dt / args.e2e_steps * 1e3,
-            "api": "lbm_set_force(host) + lbm_reset + lbm_iterate_checked + "
-                   "lbm_get_displacement/lbm_get_stress(host)",
+            "steps": args.e2e_steps, "pipeline": pipe, "ms_per_step": dt / args.e2e_steps * 1e3,
+            "api": api,
             "parts_ms": dict(zip(("set_force", "reset_iterate", "get_displacement", "get_stress"),
-                                 (float(v) for v in parts / args.e2e_steps * 1e3)))}
+                                 (float(v) for v in parts * 1e3))),
+            "parts_note": "host time per call and step, averaged over the steps"
+                          + ("; calls of different lattices overlap" if pipe > 1 else "")}
 
 
 # ---------------------------------------------------------------------------
@@ -877,7 +915,11 @@ def main():
                          "schedule, xKw on the wavefront schedule")
     ap.add_argument("--quick", action="store_true", help="skip the extra dtype variants")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-pipeline", type=int, default=1,
+                    help="lattices solved side by side in the end-to-end measurement (1: one at a time)")
+    ap.add_argument("--e2e-transfer", choices=("copy", "direct"), default="copy",
+                    help="host transfers of the side-by-side lattices (--e2e-pipeline > 1)")
     ap.add_argument("--e2e-warmup", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-n", type=int, default=1024)

@@ -116,6 +116,21 @@ void lbm_destroy(lbm_ctx *ctx);
  * all later work of this context.  The caller keeps ownership of the stream. */
 int lbm_set_stream(lbm_ctx *ctx, void *stream);
 
+/* How the calls that take host arrays (lbm_set_force, lbm_get_displacement,
+ * lbm_get_stress) move them; no counterpart in the paper.
+ *  LBM_HOST_DIRECT (default): pinned host arrays the device can address are
+ *    read or written by the library's kernels directly over the host link (no
+ *    device staging); other host arrays go through device staging by copies.
+ *  LBM_HOST_COPY: every host array goes through device staging by copies, which
+ *    the GPU's copy engines carry: a transfer then occupies no SM and overlaps
+ *    the kernels that other contexts run on other streams (several lattices
+ *    solved side by side).  Staging: up to 5 nx*ny doubles of device memory.
+ * Both give the same values.
+ * Errors: LBM_ERR_ARG (mode not one of lbm_host_transfer). */
+enum lbm_host_transfer { LBM_HOST_DIRECT = 0, LBM_HOST_COPY = 1 };
+int lbm_set_host_transfer(lbm_ctx *ctx, int mode);
+int lbm_get_host_transfer(lbm_ctx *ctx, int *mode);
+
 /* Pseudo-time steps per stream-collide launch: 1 to 4.  With k > 1, one
  * launch runs k consecutive steps of Algorithm 1 (Sec. 3.3, Eqs. collision and
  * streaming): the intermediate post-collision states stay on chip in FP32, so
@@ -123,8 +138,9 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
  * this runs on tiles (the tile and a halo of one node per extra step in shared
  * memory); four steps need the wavefront schedule (lbm_set_wavefront), and
  * without it k = 4 runs as k = 3.  A residual check (lbm_iterate_checked,
- * lbm_solve) falls on the last step of a launch of at most two steps; steps
- * left over when n is not a multiple of k run in shorter launches.  With LBM_F32 storage the
+ * lbm_solve) falls on the last step of a launch: of a four-step wavefront
+ * launch where that schedule runs, else of a launch of at most two steps;
+ * steps left over when n is not a multiple of k run in shorter launches.  With LBM_F32 storage the
  * arithmetic per node is unchanged and the state after every launch equals
  * that of the same steps taken one per launch, bit for bit.  With LBM_F16S
  * storage the intermediate states are not rounded to the FP16 storage format,
@@ -161,8 +177,9 @@ int lbm_get_wavefront(lbm_ctx *ctx, int *rows);
 /* Body force (constant in pseudo-time, Sec. 2.1).  gx, gy: host arrays of
  * nx*ny doubles (lattice units), copied.  Pinned host arrays the device can
  * address (cudaHostAlloc / cudaMallocHost, or registered mapped memory) are
- * read by the conversion kernel directly over the host link; other host
- * arrays go through a device staging copy.  The force must be finite; the
+ * read by the conversion kernel directly over the host link, unless
+ * lbm_set_host_transfer chose LBM_HOST_COPY; other host arrays go through a
+ * device staging copy.  The force must be finite; the
  * steady state exists for a zero-mean force (the mean of u is conserved,
  * Sec. 6.2), which is the caller's responsibility.  For LBM_F16S a change of
  * the force magnitude rescales the stored deviations.  Synchronous. */
@@ -320,8 +337,9 @@ const char *lbm_last_error(void);
  * pair of steps; lbm_set_steps_per_launch describes the arithmetic) or, when
  * check_every is a multiple of 4, the wavefront chunk LBM_TILE_WAVE: problems
  * at least 256 columns wide and 8 rows high advance four steps per visit of a
- * wavefront item (a 256-column strip by 64 rows on the schedule of
- * lbm_set_wavefront), narrower ones two steps per two-step tile, with two grid
+ * wavefront item (a 256-column strip by up to 256 rows on the schedule of
+ * lbm_set_wavefront; the rows are halved, down to 16, while the work list
+ * would hold fewer than four waves of resident blocks), narrower ones two steps per two-step tile, with two grid
  * barriers per four steps and items taken from a work counter, wavefront
  * items first.  Every tile code computes the same per-node arithmetic; FP32
  * results are the same bits under every code.

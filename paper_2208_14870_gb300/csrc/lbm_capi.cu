@@ -79,6 +79,7 @@ struct lbm_ctx {
     int64_t nblocks = 0;           // grid of the residual-check launch
     int spl = 1;                   // pseudo-time steps per stream-collide launch (1 to 4)
     int wave = 0;                  // launches of three or four steps: 0 tile kernel, > 0 wavefront
+    int host_transfer = LBM_HOST_DIRECT;   // lbm_host_transfer
                                    // kernel with segments of this many rows per block, -1 wavefront
                                    // with the segment chosen per launch (wave_seg)
     int nsm = 0;                   // multiprocessors of the device
@@ -649,13 +650,32 @@ int lbm_set_stream(lbm_ctx* c, void* stream) {
     return LBM_OK;
 }
 
+int lbm_set_host_transfer(lbm_ctx* c, int mode) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (mode != LBM_HOST_DIRECT && mode != LBM_HOST_COPY)
+        return fail(LBM_ERR_ARG, "lbm_set_host_transfer: mode must be LBM_HOST_DIRECT or LBM_HOST_COPY");
+    c->host_transfer = mode;
+    return LBM_OK;
+}
+
+int lbm_get_host_transfer(lbm_ctx* c, int* mode) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!mode) return fail(LBM_ERR_ARG, "lbm_get_host_transfer: null pointer");
+    *mode = c->host_transfer;
+    return LBM_OK;
+}
+
 int lbm_set_force(lbm_ctx* c, const double* gx, const double* gy) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!gx || !gy) return fail(LBM_ERR_ARG, "lbm_set_force: null pointer");
     // pinned, mapped host arrays: read by the conversion kernel directly
-    const void* mx = mapped_host(gx);
-    const void* my = mapped_host(gy);
+    // (LBM_HOST_DIRECT), else copied into device staging
+    const bool direct = c->host_transfer == LBM_HOST_DIRECT;
+    const void* mx = direct ? mapped_host(gx) : nullptr;
+    const void* my = direct ? mapped_host(gy) : nullptr;
     if (mx && my) return set_force_dev(c, static_cast<const double*>(mx), static_cast<const double*>(my));
     rc = ensure_staging(c, 2 * c->n);
     if (rc) return rc;
@@ -906,11 +926,11 @@ int lbm_get_fields_device(lbm_ctx* c, double* out) {
 namespace {
 
 // Host field getters: into pinned, mapped host arrays the recovery kernel
-// writes directly (only the requested fields); other host arrays receive
-// copies of the fields staged once per state.
+// writes directly (only the requested fields; LBM_HOST_DIRECT); other host
+// arrays receive copies of the fields staged once per state.
 int get_fields_host(lbm_ctx* c, int first, int count, double* const* dst) {
     FieldOut o{};
-    bool mapped = true;
+    bool mapped = c->host_transfer == LBM_HOST_DIRECT;
     for (int k = 0; k < count && mapped; ++k) {
         o.p[first + k] = static_cast<double*>(const_cast<void*>(mapped_host(dst[k])));
         mapped = o.p[first + k] != nullptr;

@@ -928,9 +928,14 @@ k_step3(const StepParams a, const Coef<float> c) {
 #ifndef LBM_WV_NW
 #define LBM_WV_NW 8
 #endif
-// FP32 step 1: populations loaded two rows ahead (1) or one (0)
+// step 1: populations loaded two rows ahead (1) or one (0), per storage type
+// (FP16S pulls hold three times the registers; two rows ahead measured 1 %
+// slower)
 #ifndef LBM_WV_LA2_F32
 #define LBM_WV_LA2_F32 1
+#endif
+#ifndef LBM_WV_LA2_F16S
+#define LBM_WV_LA2_F16S 0
 #endif
 constexpr int kWvNW = LBM_WV_NW;                 // warps per block
 constexpr int kWvW = 32 * kWvNW;                 // strip width (slot columns)
@@ -939,7 +944,24 @@ constexpr int kWvD = 4;                          // ring rows per level
 constexpr int kWvRP = 6;                         // populations held in a ring (all but 2 and 4)
 constexpr int kWvSegDefault = 256;               // output rows per block segment (default)
 template <int S>
-__host__ __device__ constexpr bool wv_la2() { return S == S_F32 && LBM_WV_LA2_F32 != 0; }
+__host__ __device__ constexpr bool wv_la2() {
+    return S == S_F16S ? LBM_WV_LA2_F16S != 0 : LBM_WV_LA2_F32 != 0;
+}
+// step 1 collides its row at the start of the iteration (1), so its decoded
+// populations die before the other levels run and its load buffers are free
+// for the next row, or after the other levels (0), so its loads are issued
+// earlier.  Defaults: the faster at 16384^2 on GB300 (FP32 after: 3.34 against
+// 3.77 ms per four-step launch; FP16S first: 3.48 against 3.72 ms)
+#ifndef LBM_WV_L1FIRST_F32
+#define LBM_WV_L1FIRST_F32 0
+#endif
+#ifndef LBM_WV_L1FIRST_F16S
+#define LBM_WV_L1FIRST_F16S 1
+#endif
+template <int S>
+__host__ __device__ constexpr bool wv_l1first() {
+    return S == S_F16S ? LBM_WV_L1FIRST_F16S != 0 : LBM_WV_L1FIRST_F32 != 0;
+}
 static_assert(kWvW <= kThreads, "residual_reduce sizes its scratch by kThreads");
 template <int T> __host__ __device__ constexpr int wv_ox() { return kWvW - 2 * (T - 1); }
 template <int S, int T> __host__ __device__ constexpr int wv_smem() {
@@ -966,6 +988,7 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     static_assert(T >= 2 && T <= 4, "two to four steps per launch");
     constexpr int W = kWvW, R = kWvRow, OX = wv_ox<T>(), PL = kWvD * kWvRow, RP = kWvRP * PL, D = kWvD - 1;
     constexpr bool PA2 = wv_la2<S>();             // populations two rows ahead
+    constexpr bool L1FIRST = wv_l1first<S>();     // step 1 collides before the other levels
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
     const int xs = strip * OX - (T - 1) + t;      // lattice column of slot t (unwrapped)
@@ -1002,7 +1025,7 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     // ahead, else one) in registers.  The row offsets of the next row to load
     // advance one row per load (rows are loaded in order), with the periodic
     // wrap.
-    constexpr bool LA2 = S == S_F32;
+    constexpr bool LA2 = S == S_F32 || PA2;
     Pulled<S> q[PA2 ? 2 : 1];
     float qg[LA2 ? 2 : 1][2];
     int ly = wrap_slot<false>(ybeg, ny);          // lattice row of the next population load
@@ -1047,10 +1070,28 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
         }
         hx[0] = qg[b][0];
         hy[0] = qg[b][1];
-        float f1[8];
+        // step 1 on local row i: its populations 2 and 4 (t2, t4) enter the
+        // delay lines after the levels below have read them
+        float f1[8], t2 = 0.0f, t4 = 0.0f;
+        auto level1 = [&]() {
+            float u, v, fs[8];
+            collide_populations<GEN>(moments(f1), hx[0], hy[0], c, u, v, fs);
+            float* d = rt + (i & D) * R;
+            d[0 * PL] = fs[0];
+            d[1 * PL] = fs[2];
+            d[2 * PL] = fs[4];
+            d[3 * PL] = fs[5];
+            d[4 * PL] = fs[6];
+            d[5 * PL] = fs[7];
+            t2 = fs[1];
+            t4 = fs[3];
+        };
         if (l1) {
             constexpr int bq = PA2 ? b : 0;
             pull_decode<S>(a, q[bq], f1, c.theta);
+            // L1FIRST: collide row i before reloading its buffers (ring slot i
+            // mod 4 is not among the slots the levels below read)
+            if constexpr (L1FIRST) level1();
             if (FULL || i + (PA2 ? 2 : 1) < n1) load1(bq);
             if (FULL || i + (LA2 ? 2 : 1) < n1) load_force(b);
         }
@@ -1102,19 +1143,11 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
             }
         }
         if (l1) {
-            float u, v, fs[8];
-            collide_populations<GEN>(moments(f1), hx[0], hy[0], c, u, v, fs);
-            float* d = rt + (i & D) * R;
-            d[0 * PL] = fs[0];
-            d[1 * PL] = fs[2];
-            d[2 * PL] = fs[4];
-            d[3 * PL] = fs[5];
-            d[4 * PL] = fs[6];
-            d[5 * PL] = fs[7];
+            if constexpr (!L1FIRST) level1();
             v2[0][2] = v2[0][1];
             v2[0][1] = v2[0][0];
-            v2[0][0] = fs[1];
-            v4[0] = fs[3];
+            v2[0][0] = t2;
+            v4[0] = t4;
         }
         __syncthreads();
     };

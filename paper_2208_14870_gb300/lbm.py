@@ -57,6 +57,8 @@ _SIGS = {
                                  _c.POINTER(lbm_options), _c.POINTER(_vp)]),
     "lbm_destroy": (None, [_vp]),
     "lbm_set_stream": (_c.c_int, [_vp, _vp]),
+    "lbm_set_host_transfer": (_c.c_int, [_vp, _c.c_int]),
+    "lbm_get_host_transfer": (_c.c_int, [_vp, _c.POINTER(_c.c_int)]),
     "lbm_set_steps_per_launch": (_c.c_int, [_vp, _c.c_int]),
     "lbm_get_steps_per_launch": (_c.c_int, [_vp, _c.POINTER(_c.c_int)]),
     "lbm_set_wavefront": (_c.c_int, [_vp, _c.c_int]),
@@ -151,6 +153,16 @@ def lbm_destroy(ctx: int) -> None:
 
 def lbm_set_stream(ctx: int, stream: int) -> None:
     _check(_lib.lbm_set_stream(ctx, stream), "lbm_set_stream")
+
+
+def lbm_set_host_transfer(ctx: int, mode: int) -> None:
+    _check(_lib.lbm_set_host_transfer(ctx, mode), "lbm_set_host_transfer")
+
+
+def lbm_get_host_transfer(ctx: int) -> int:
+    m = _c.c_int()
+    _check(_lib.lbm_get_host_transfer(ctx, _c.byref(m)), "lbm_get_host_transfer")
+    return m.value
 
 
 def lbm_set_steps_per_launch(ctx: int, k: int) -> None:
@@ -284,6 +296,8 @@ def lbm_get_device_bytes(ctx: int) -> int:
 LBM_NOALLOC_MAX_BLOCKS = 1024
 LBM_TILE_TWO_STEP = 3
 LBM_TILE_WAVE = 5
+LBM_HOST_DIRECT = 0
+LBM_HOST_COPY = 1
 
 
 def lbm_step_checked_noalloc(nx: int, ny: int, lam: float, mu: float, dtype: int, f_src: int,
@@ -362,6 +376,14 @@ class Lattice:
 
     def set_stream(self, stream_handle: int):
         lbm_set_stream(self.ctx, stream_handle)
+
+    @property
+    def host_transfer(self) -> int:
+        return lbm_get_host_transfer(self.ctx)
+
+    @host_transfer.setter
+    def host_transfer(self, mode: int):
+        lbm_set_host_transfer(self.ctx, mode)
 
     def set_force(self, gx, gy):
         """Host numpy arrays (copied) or device torch tensors (float64)."""

@@ -420,3 +420,70 @@ def test_pinned_and_pageable_host_buffers_agree(dtype):
             with pytest.raises(P.LBMError):
                 P.lbm_set_force(lat.ctx, bad.data_ptr(), pgy.data_ptr())
     assert np.array_equal(out[0], out[1])
+
+
+def _pinned_solve(nx, ny, lam, mu, dtype, pgx, pgy, steps, mode, stream=None):
+    """Force from pinned arrays, `steps` steps, the five fields into pinned
+    arrays, with host transfer `mode` (optionally on its own stream)."""
+    with Lattice(nx, ny, lam, mu, dtype) as lat:
+        if stream is not None:
+            lat.set_stream(stream.cuda_stream)
+        lat.host_transfer = mode
+        assert lat.host_transfer == mode
+        P.lbm_set_force(lat.ctx, pgx.data_ptr(), pgy.data_ptr())
+        lat.iterate(steps)
+        f = [torch.empty(nx * ny, dtype=torch.float64).pin_memory() for _ in range(5)]
+        P.lbm_get_displacement(lat.ctx, f[0].data_ptr(), f[1].data_ptr())
+        P.lbm_get_stress(lat.ctx, f[2].data_ptr(), f[3].data_ptr(), f[4].data_ptr())
+        return np.stack([t.numpy().reshape(ny, nx) for t in f])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_host_copy_mode_agrees_with_direct(dtype):
+    """LBM_HOST_COPY moves pinned host arrays by copies through device staging
+    instead of kernels that read and write them over the host link: the same
+    bits; an unknown mode is rejected."""
+    lam, mu = W.lame_2d(1.0, 0.3)
+    nx, ny = 300, 70
+    gx, gy = W.random_force_grid(W.random_force(nx, ny, 6, 4, seed=98))
+    pgx = torch.from_numpy(gx.copy()).pin_memory()
+    pgy = torch.from_numpy(gy.copy()).pin_memory()
+    a = _pinned_solve(nx, ny, lam, mu, dtype, pgx, pgy, 41, P.LBM_HOST_DIRECT)
+    b = _pinned_solve(nx, ny, lam, mu, dtype, pgx, pgy, 41, P.LBM_HOST_COPY)
+    assert np.array_equal(a, b)
+    with Lattice(8, 8, lam, mu, dtype) as lat:
+        with pytest.raises(P.LBMError):
+            lat.host_transfer = 2
+
+
+def test_two_lattices_on_two_streams_from_two_threads():
+    """Two lattices on their own streams, driven from two host threads with
+    copy-engine transfers (the pipelined end-to-end form of the benchmark):
+    each gives the bits it gives alone."""
+    import threading
+    lam, mu = W.lame_2d(1.0, 0.3)
+    nx, ny = 512, 260
+    cases = []
+    for seed in (11, 12):
+        gx, gy = W.random_force_grid(W.random_force(nx, ny, 8, 4, seed=seed))
+        cases.append((torch.from_numpy(gx.copy()).pin_memory(), torch.from_numpy(gy.copy()).pin_memory()))
+    alone = [_pinned_solve(nx, ny, lam, mu, "f32", gx, gy, 64, P.LBM_HOST_COPY) for gx, gy in cases]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    got = [None, None]
+    errors = []
+
+    def run(k):
+        try:
+            for _ in range(3):
+                got[k] = _pinned_solve(nx, ny, lam, mu, "f32", *cases[k], 64, P.LBM_HOST_COPY, streams[k])
+        except Exception as e:  # pragma: no cover - reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for k in range(2):
+        assert np.array_equal(got[k], alone[k])
