@@ -35,8 +35,10 @@ def _run(nx, ny, dtype, spl, wave, steps, seed, check_every=None, **kw):
 
 
 # (256, 8): one strip, the smallest lattice on the schedule; the others leave
-# a ragged last strip and/or segment.
-@pytest.mark.parametrize("nx,ny", [(256, 8), (256, 45), (293, 40), (509, 23), (763, 13), (1000, 77)])
+# a ragged last strip and/or segment (268, 500: the last strip reaches past
+# the lattice's x period by a few to 247 columns).
+@pytest.mark.parametrize("nx,ny", [(256, 8), (256, 45), (293, 40), (509, 23), (763, 13), (1000, 77),
+                                   (264, 8), (268, 9), (500, 16), (752, 33)])
 @pytest.mark.parametrize("T", [3, 4])
 @pytest.mark.parametrize("seg", [1, 7, 128, -1])
 @pytest.mark.parametrize("steps", [None, 11])
