@@ -615,7 +615,7 @@ def run_e2e(args, gx, gy, torch, P, ws, dist):
         if pipe > 1:
             stream = torch.cuda.Stream()
             lat.set_stream(stream.cuda_stream)
-            lat.host_transfer = P.LBM_HOST_COPY if args.e2e_transfer == "copy" else P.LBM_HOST_DIRECT
+        lat.host_transfer = P.LBM_HOST_COPY if args.e2e_transfer == "copy" else P.LBM_HOST_DIRECT
         outs = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(5)]
         lanes.append({"lat": lat, "stream": stream, "outs": outs, "res": np.zeros(5), "parts": np.zeros(4)})
 
@@ -673,9 +673,9 @@ def run_e2e(args, gx, gy, torch, P, ws, dist):
     api = ("lbm_set_force(host) + lbm_reset + lbm_iterate_checked + "
            "lbm_get_displacement/lbm_get_stress(host)")
     if pipe > 1:
-        api += ", %d lattices on their own streams, one host thread each, %s" % (
-            pipe, "LBM_HOST_COPY (copy-engine transfers)" if args.e2e_transfer == "copy"
-            else "LBM_HOST_DIRECT (kernels read and write the pinned host arrays)")
+        api += ", %d lattices on their own streams, one host thread each" % pipe
+    api += ", " + ("LBM_HOST_COPY (copy-engine transfers through device staging)" if args.e2e_transfer == "copy"
+                   else "LBM_HOST_DIRECT (kernels read and write the pinned host arrays)")
     return {"value": float(n) * n * args.iters * args.e2e_steps * ws / dt / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 5 * n * n * 8 + 5 * 8,
             "steps": args.e2e_steps, "pipeline": pipe, "ms_per_step": dt / args.e2e_steps * 1e3,
@@ -918,8 +918,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--e2e-pipeline", type=int, default=1,
                     help="lattices solved side by side in the end-to-end measurement (1: one at a time)")
-    ap.add_argument("--e2e-transfer", choices=("copy", "direct"), default="copy",
-                    help="host transfers of the side-by-side lattices (--e2e-pipeline > 1)")
+    ap.add_argument("--e2e-transfer", choices=("copy", "direct"), default="direct",
+                    help="host transfers of the end-to-end measurement (lbm_set_host_transfer)")
     ap.add_argument("--e2e-warmup", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-n", type=int, default=1024)
