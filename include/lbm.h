@@ -342,7 +342,13 @@ const char *lbm_last_error(void);
  * would hold fewer than four waves of resident blocks), narrower ones two steps per two-step tile, with two grid
  * barriers per four steps and items taken from a work counter, wavefront
  * items first.  Every tile code computes the same per-node arithmetic; FP32
- * results are the same bits under every code.
+ * results are the same bits under every code.  A problem that fits these
+ * tiles clearly better with x and y exchanged (narrow and tall, or a width just
+ * past a multiple of the strip's 250 output columns) is solved on its
+ * transpose: the scheme is symmetric under the exchange (u_x <-> u_y, sigma_xx
+ * <-> sigma_yy), the outputs are returned in the caller's orientation and
+ * lbm_result.transposed reports it; the result then equals the problem solved
+ * as given up to rounding.
  * ------------------------------------------------------------------------- */
 /* Tile codes in lbm_batch_report.tile_v and lbm_stats.tile_v besides the
  * widths 1, 2, 4: two-step tiles, and the wavefront chunk. */
@@ -362,6 +368,10 @@ typedef struct lbm_result {
     double residual;            /* last r_inf of the problem */
     double *ux, *uy;            /* host outputs, nx*ny each, caller-owned; may be null */
     double *sxx, *syy, *sxy;    /* host outputs (lattice-unit stress); may be null */
+    int transposed;             /* out: 1 if the problem was solved on its transpose (x and y
+                                   exchanged, a schedule choice for lattices that fit the
+                                   arena's tiles better that way; the outputs are in the
+                                   caller's orientation and differ only in rounding) */
 } lbm_result;
 
 typedef struct lbm_batch_report {

@@ -120,6 +120,24 @@ constexpr int kArenaWaveSegMax = 256;
 // (wavefront items address a problem with 32-bit in-plane offsets)
 inline bool arena_wide(int nx, int ny) { return wave_fits(nx, ny) && (int64_t)nx * ny < (int64_t(1) << 31); }
 
+// Relative device work per lattice update of an nx x ny problem in the
+// wavefront chunk: a wide problem pays for the slot columns of its 256-column
+// strips; a narrower one runs two-step tiles, at about half the wavefront's
+// rate on a large lattice (GB300: 159 against 308 GLUPS), and pays for the
+// slots of its tiles.
+inline double arena_cost(int nx, int ny) {
+    if (arena_wide(nx, ny)) return double((nx + wv_ox<4>() - 1) / wv_ox<4>()) * kWvW / nx;
+    return 1.94 * (double((nx + kT2OX - 1) / kT2OX) * kT2W / nx) * (double((ny + kT2OY - 1) / kT2OY) * kT2H / ny);
+}
+
+// Solve a problem on its transpose (x and y exchanged) where that is clearly
+// cheaper.  The scheme is symmetric under the exchange (velocities (c_x, c_y)
+// -> (c_y, c_x) map the moments 10 <-> 01, 12 <-> 21, s -> s, d -> -d, 11 ->
+// 11, 22 -> 22 onto each other; Table 1 and the rates with w_12 = w_21 follow),
+// so the transposed problem's solution is the solution's transpose with u_x
+// <-> u_y and sigma_xx <-> sigma_yy; only the rounding order differs.
+inline bool arena_transpose(int nx, int ny) { return arena_cost(ny, nx) < 0.95 * arena_cost(nx, ny); }
+
 // Number of tiles of an nx x ny problem for tile code V (seg: rows per
 // wavefront item of the wavefront chunk).
 inline int64_t arena_tiles(int nx, int ny, int V, int seg = kArenaWaveSegMax) {

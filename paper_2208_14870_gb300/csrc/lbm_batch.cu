@@ -135,6 +135,7 @@ extern "C" int lbm_batch_solve(int count, const lbm_problem* probs, int dtype, d
                 r.status = hp.status;
                 r.iters = hp.steps;
                 r.residual = hp.residual;
+                r.transposed = hp.tr ? 1 : 0;
                 lups += hp.lups;
                 double* o[5] = {r.ux, r.uy, r.sxx, r.syy, r.sxy};
                 if (!(o[0] || o[1] || o[2] || o[3] || o[4])) continue;

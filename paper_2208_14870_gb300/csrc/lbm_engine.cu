@@ -146,6 +146,9 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
         if (dtype_ == S_F16S) acar_.release(p.car_off, p.car_bytes);
         return -1;
     }
+    // a problem that is cheaper on its transpose is solved there: lattice
+    // ny x nx, force components exchanged, node (x, y) at x * ny + y
+    const bool tr = arena_transpose(nx, ny);
     // force -> FP32 staging (pinned), with the FP16 scale from its maximum
     if (h_force_cap_ < 2 * n) {
         if (h_force_) {
@@ -168,9 +171,16 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
             return LBM_ERR_ARG;
         }
         gmax = std::fmax(gmax, std::fmax(std::fabs(a), std::fabs(b)));
-        h_force_[i] = (float)a;
-        h_force_[n + i] = (float)b;
+        if (tr) {
+            const int64_t t = (i % nx) * ny + i / nx;
+            h_force_[t] = (float)b;
+            h_force_[n + t] = (float)a;
+        } else {
+            h_force_[i] = (float)a;
+            h_force_[n + i] = (float)b;
+        }
     }
+    if (tr) std::swap(nx, ny);
     p.hexp = dtype_ == S_F16S ? f16s_exponent(gmax, nx, ny) : 0;
     if (p.hexp != 0) {
         // FP16S keeps its state, the force included, in units scaled by 2^hexp
@@ -185,6 +195,7 @@ int ArenaEngine::admit(int nx, int ny, double lambda, double mu, const double* g
     p.parity = 0;
     p.nx = nx;
     p.ny = ny;
+    p.tr = tr;
     p.n = n;
     p.lambda = lambda;
     p.mu = mu;
@@ -478,8 +489,16 @@ cudaError_t ArenaEngine::launch_fields(int slot, double* dst) {
     c.bs = 1.0 - 0.5 * ws;
     c.bd = 1.0 - 0.5 * wd;
     c.theta = theta;
-    return dtype_ == S_F16S ? Ops<S_F16S>::fields(a, c, (float)theta, field_planes(dst, p.n), st_)
-                            : Ops<S_F32>::fields(a, c, (float)theta, field_planes(dst, p.n), st_);
+    FieldOut o = field_planes(dst, p.n);
+    if (p.tr) {
+        // back to the caller's lattice: u_x <-> u_y, sigma_xx <-> sigma_yy,
+        // node (x, y) of the transpose at x * ny + y
+        std::swap(o.p[0], o.p[1]);
+        std::swap(o.p[2], o.p[3]);
+        o.tr = 1;
+    }
+    return dtype_ == S_F16S ? Ops<S_F16S>::fields(a, c, (float)theta, o, st_)
+                            : Ops<S_F32>::fields(a, c, (float)theta, o, st_);
 }
 
 int ArenaEngine::ensure_fields_buffer(int64_t len, std::string* err) {

@@ -17,7 +17,8 @@ enum ProbState { P_FREE = 0, P_RUNNING = 1, P_DONE = 2 };
 
 struct HostProb {
     int state = P_FREE;
-    int nx = 0, ny = 0;
+    int nx = 0, ny = 0;            // the arena lattice (the caller's, or its transpose)
+    bool tr = false;               // solved transposed (arena_transpose)
     int64_t n = 0;
     double lambda = 0.0, mu = 0.0;
     int64_t pop_off = -1, car_off = -1, fs_off = -1;

@@ -1198,13 +1198,17 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
 // sigma_xy (nx*ny doubles each; a null entry is not written).  Device memory,
 // or pinned host memory the device can address (the recovery then writes the
 // caller's arrays over the host link directly).
+// tr: the lattice is the transpose of the caller's (x and y exchanged), so
+// node (x, y) goes to entry x * ny + y of each destination.
 struct FieldOut {
     double* p[5];
+    int tr;
 };
 
 inline FieldOut field_planes(double* out, int64_t n) {
     FieldOut o;
     for (int k = 0; k < 5; ++k) o.p[k] = out + k * n;
+    o.tr = 0;
     return o;
 }
 
@@ -1254,11 +1258,12 @@ k_fields(const StepParams a, const Coef<double> c, typename StoreT<S>::T theta, 
     // (FP16S: back from the state's scaled units, a power of two)
     const double un = S == S_F16S ? (double)a.hinv : 1.0;
     const double mb11 = c.b11 * m11, mbs = c.bs * ms, mbd = c.bd * md;
-    if (out.p[0]) out.p[0][idx] = u * un;
-    if (out.p[1]) out.p[1][idx] = v * un;
-    if (out.p[2]) out.p[2][idx] = -0.5 * (mbs + mbd) * un;
-    if (out.p[3]) out.p[3][idx] = -0.5 * (mbs - mbd) * un;
-    if (out.p[4]) out.p[4][idx] = -mb11 * un;
+    const int64_t o = out.tr ? (int64_t)x * ny + y : idx;
+    if (out.p[0]) out.p[0][o] = u * un;
+    if (out.p[1]) out.p[1][o] = v * un;
+    if (out.p[2]) out.p[2][o] = -0.5 * (mbs + mbd) * un;
+    if (out.p[3]) out.p[3][o] = -0.5 * (mbs - mbd) * un;
+    if (out.p[4]) out.p[4][o] = -mb11 * un;
 }
 
 // Pre-collision populations of the current state into 8 FP64 planes.

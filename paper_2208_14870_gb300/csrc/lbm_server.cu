@@ -45,6 +45,7 @@ struct Request {
     int status = LBM_OK;
     int64_t iters = 0;
     double residual = 0.0;
+    int transposed = 0;
     clk::time_point t_submit, t_admit, t_done;
     int arena = 0, slot = -1;
     int64_t bypassed = 0;         // chunks during which later requests were admitted first
@@ -218,6 +219,7 @@ void lbm_server::retire(int a, const std::vector<int>& slots, std::unique_lock<s
         r.status = rc != LBM_OK ? rc : p.status;
         r.iters = p.steps;
         r.residual = p.residual;
+        r.transposed = p.tr ? 1 : 0;
         lups += p.lups;
         arena[a]->release(slot);
         slot_owner[a].erase(slot);
@@ -343,6 +345,7 @@ static int take_result(lbm_server* s, Request& r, lbm_result* out) {
         out->status = r.status;
         out->iters = r.iters;
         out->residual = r.residual;
+        out->transposed = r.transposed;
         const int64_t n = (int64_t)r.nx * r.ny;
         double* dst[5] = {out->ux, out->uy, out->sxx, out->syy, out->sxy};
         if (!r.fields.empty())

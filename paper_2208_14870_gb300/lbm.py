@@ -500,7 +500,8 @@ class lbm_problem(ctypes.Structure):
 
 class lbm_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int64), ("residual", ctypes.c_double),
-                ("ux", _vp), ("uy", _vp), ("sxx", _vp), ("syy", _vp), ("sxy", _vp)]
+                ("ux", _vp), ("uy", _vp), ("sxx", _vp), ("syy", _vp), ("sxy", _vp),
+                ("transposed", ctypes.c_int)]
 
 
 class lbm_batch_report(ctypes.Structure):
@@ -519,7 +520,8 @@ def batch_solve(problems, dtype: str = "f32", tol: float = 1e-8, check_every: in
                 max_iters: int = 10_000_000, fields: bool = True):
     """Solve many problems in one arena.  ``problems``: iterable of
     (nx, ny, lam, mu, gx, gy) with host FP64 arrays.  Returns (results, report):
-    results is a list of dicts (status, iters, residual[, fields (5, ny, nx)])."""
+    results is a list of dicts (status, iters, residual, transposed[, fields
+    (5, ny, nx)])."""
     problems = list(problems)
     cnt = len(problems)
     arr = (lbm_problem * cnt)()
@@ -542,7 +544,8 @@ def batch_solve(problems, dtype: str = "f32", tol: float = 1e-8, check_every: in
                                 ctypes.byref(rep)), "lbm_batch_solve")
     results = []
     for i in range(cnt):
-        d = {"status": res[i].status, "iters": res[i].iters, "residual": res[i].residual}
+        d = {"status": res[i].status, "iters": res[i].iters, "residual": res[i].residual,
+             "transposed": bool(res[i].transposed)}
         if fields:
             d["fields"] = outs[i]
         results.append(d)
@@ -636,7 +639,8 @@ class Server:
             return None
         _check(st, fn.__name__)
         del self._shapes[ticket]
-        d = {"status": res.status, "iters": res.iters, "residual": res.residual}
+        d = {"status": res.status, "iters": res.iters, "residual": res.residual,
+             "transposed": bool(res.transposed)}
         if fields:
             d["fields"] = out
         return d

@@ -101,8 +101,8 @@ def test_kernel_hash_ignores_comments_but_not_code(bench, tmp_path):
     assert bench.kernel_hash(lambda n: changed[n]) != base
     # the field recovery is not part of the stream-collide kernels
     later = dict(files)
-    later["lbm_kernels.cuh"] = files["lbm_kernels.cuh"].replace("if (out.p[4]) out.p[4][idx] = -mb11 * un;",
-                                                                 "if (out.p[4]) out.p[4][idx] = -1.0 * mb11 * un;")
+    later["lbm_kernels.cuh"] = files["lbm_kernels.cuh"].replace("if (out.p[4]) out.p[4][o] = -mb11 * un;",
+                                                                 "if (out.p[4]) out.p[4][o] = -1.0 * mb11 * un;")
     assert later["lbm_kernels.cuh"] != files["lbm_kernels.cuh"]
     assert bench.kernel_hash(lambda n: later[n]) == base
 

@@ -36,6 +36,23 @@ SIZES = [(33, 17), (64, 64), (130, 7), (40, 96), (1, 9), (200, 150), (77, 77), (
          (128, 128), (5, 5), (250, 31), (96, 40)]
 
 
+def single_fields(nx, ny, lam, mu, gx, gy, steps, transposed, dtype="f32"):
+    """The single-lattice path after `steps` steps, in the orientation the
+    arena solved the problem in: on its transpose (lattice ny x nx, force
+    components exchanged) the fields come back transposed with u_x <-> u_y and
+    sigma_xx <-> sigma_yy."""
+    if not transposed:
+        with P.Lattice(nx, ny, lam, mu, dtype) as lat:
+            lat.set_force(gx, gy)
+            lat.iterate(steps)
+            return lat.fields()
+    with P.Lattice(ny, nx, lam, mu, dtype) as lat:
+        lat.set_force(np.ascontiguousarray(gy.T), np.ascontiguousarray(gx.T))
+        lat.iterate(steps)
+        f = lat.fields()
+    return np.stack([f[1].T, f[0].T, f[3].T, f[2].T, f[4].T])
+
+
 def make_problems(sizes, seed=0):
     probs = []
     rng = W.SplitMix64(seed)
@@ -156,10 +173,8 @@ def test_batch_wavefront_chunk_matches_single_lattice(monkeypatch):
     assert report["tile_v"] == P.LBM_TILE_WAVE
     for (nx, ny, lam, mu, gx, gy, pw), r in zip(probs, results):
         assert r["status"] == P.LBM_ERR_NOT_CONVERGED and r["iters"] == 300
-        with P.Lattice(nx, ny, lam, mu, "f32") as lat:
-            lat.set_force(gx, gy)
-            lat.iterate(300)
-            assert np.array_equal(r["fields"], lat.fields()), (nx, ny)
+        ref = single_fields(nx, ny, lam, mu, gx, gy, 300, r["transposed"])
+        assert np.array_equal(r["fields"], ref), (nx, ny)
 
 
 def test_batch_recovery_packs_small_and_large_problems():
@@ -173,10 +188,35 @@ def test_batch_recovery_packs_small_and_large_problems():
                                max_iters=200)
     for (nx, ny, lam, mu, gx, gy, pw), r in zip(probs, results):
         assert r["status"] == P.LBM_ERR_NOT_CONVERGED and r["iters"] == 200
-        with P.Lattice(nx, ny, lam, mu, "f32") as lat:
-            lat.set_force(gx, gy)
-            lat.iterate(200)
-            assert np.array_equal(r["fields"], lat.fields()), (nx, ny)
+        ref = single_fields(nx, ny, lam, mu, gx, gy, 200, r["transposed"])
+        assert np.array_equal(r["fields"], ref), (nx, ny)
     res_nf, _ = P.batch_solve([p[:6] for p in probs], dtype="f32", tol=0.0, check_every=100,
                               max_iters=200, fields=False)
     assert all("fields" not in r and r["iters"] == 200 for r in res_nf)
+
+
+# (nx, ny, solved transposed): a narrow, tall lattice runs on its transpose
+# (wavefront items instead of two-step tiles); one just wider than a strip
+# (260 of 250 output columns) but tall does too; wide or square ones do not.
+ORIENT = [(100, 700, True), (64, 520, True), (260, 1000, True), (700, 100, False), (300, 300, False),
+          (1000, 260, False), (40, 30, False)]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16s"])
+def test_batch_solves_narrow_tall_problems_transposed(dtype):
+    """Problems that fit the arena better on their transpose are solved there:
+    FP32 results are the bits of the single-lattice path on the transposed
+    problem (force components exchanged, fields transposed back with u_x <->
+    u_y and sigma_xx <-> sigma_yy), and within rounding of the problem solved
+    as given; FP16S within its storage tolerance of the latter."""
+    probs = make_problems([(nx, ny) for nx, ny, _ in ORIENT], seed=23)
+    results, _ = P.batch_solve([p[:6] for p in probs], dtype=dtype, tol=0.0, check_every=100, max_iters=400)
+    for (nx, ny, tr), (_, _, lam, mu, gx, gy, pw), r in zip(ORIENT, probs, results):
+        assert r["status"] == P.LBM_ERR_NOT_CONVERGED and r["iters"] == 400
+        assert r["transposed"] == tr, (nx, ny)
+        as_given = single_fields(nx, ny, lam, mu, gx, gy, 400, False, dtype)
+        if dtype == "f32":
+            assert np.array_equal(r["fields"], single_fields(nx, ny, lam, mu, gx, gy, 400, tr)), (nx, ny)
+            assert rel_per_field(r["fields"], as_given) < 1e-5, (nx, ny)
+        else:
+            assert rel_per_field(r["fields"], as_given) < 2e-3, (nx, ny)
