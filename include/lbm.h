@@ -125,7 +125,10 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
  *    the GPU's copy engines carry: a transfer then occupies no SM and overlaps
  *    the kernels that other contexts run on other streams (several lattices
  *    solved side by side).  Staging: up to 5 nx*ny doubles of device memory.
- * Both give the same values.
+ * Both give the same values.  On GB300 (16384^2, FP32) the direct route was
+ * the faster one both for one lattice and for two solved side by side: the
+ * staged field copies add a device pass, and the copies slow down beside the
+ * other lattice's kernels about as much as the direct transfers do.
  * Errors: LBM_ERR_ARG (mode not one of lbm_host_transfer). */
 enum lbm_host_transfer { LBM_HOST_DIRECT = 0, LBM_HOST_COPY = 1 };
 int lbm_set_host_transfer(lbm_ctx *ctx, int mode);
