@@ -513,7 +513,10 @@ def run_ours(args, ws, rank, local):
     ncu_util = tr.get("ncu") if current else None
 
     variants = {}
-    if not args.quick:
+    # the storage-type variants, the batched and the served workloads are
+    # single-GPU measurements: taken at N = 1 only, so that a scaling run holds
+    # its GPUs for the replicated throughput and end-to-end steps alone
+    if not args.quick and ws == 1:
         for name in args.variants:
             mt = re.fullmatch(r"(f64|f32|f16s)(?:x(\d))?(w?)", name)
             if name == args.dtype or mt is None:
@@ -549,8 +552,8 @@ def run_ours(args, ws, rank, local):
         e2e = run_e2e(args, gx, gy, torch, P, ws, dist if ws > 1 else None)
     del gx_d, gy_d
     torch.cuda.empty_cache()
-    batched = None if (args.no_batched or args.quick) else run_batched(args, P)
-    served = None if (args.no_served or args.quick) else run_served(args, P)
+    batched = None if (args.no_batched or args.quick or ws > 1) else run_batched(args, P)
+    served = None if (args.no_served or args.quick or ws > 1) else run_served(args, P)
 
     if rank == 0:
         line = {
@@ -587,7 +590,7 @@ def run_ours(args, ws, rank, local):
             "batched": batched,
             "served": served,
         }
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)
     if ws > 1:
