@@ -52,13 +52,19 @@ def rel_per_field(a, b):
     return max(eu, es)
 
 
+# (nx, ny, solved transposed): 60 x 300 fits the arena better on its transpose
+# (wavefront items instead of two-step tiles); its fields come back in the
+# caller's orientation
+@pytest.mark.parametrize("nx,ny,tr", [(96, 72, False), (60, 300, True)])
 @pytest.mark.parametrize("dtype,tol,tol_fix", [("f32", 2e-9, 2e-5), ("f16s", 2e-7, 2e-3)])
-def test_same_result_alone_and_in_the_mix(dtype, tol, tol_fix):
-    target = problem(96, 72, 0.3, seed=42)
+def test_same_result_alone_and_in_the_mix(dtype, tol, tol_fix, nx, ny, tr):
+    target = problem(nx, ny, 0.3, seed=42)
     with P.Server(2 * GIB, check_every=100) as srv:
         t = srv.submit(*target[:6], dtype=dtype, tol=tol)
         alone = srv.wait(t, 120.0)
         assert alone["status"] == P.LBM_OK
+        assert alone["transposed"] == tr
+        assert alone["fields"].shape == (5, ny, nx)
         assert srv.stats()["peak_running"] == 1
     others = [problem(int(s), int(s * 0.75) + 3, 0.05 * i, seed=100 + i)
               for i, s in enumerate([40, 200, 64, 150, 32, 128, 90, 250, 48, 180])]
