@@ -61,12 +61,12 @@ FP64_PEAK_GINST = 625.0
 # per output column) and segment length as the 16384^2 launch, so a launch's
 # traffic is 4x the capture's (nodes x4).  Mean of three launches.
 NCU_TRAFFIC = {
-    "f32_x4w": {"bytes_per_launch": 4 * (2.76158e9 + 2.10528e9), "kernel_hash": "b400427d9e6bdb2d",
-                "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.76158e9,
-                        "dram_write_per_launch": 4 * 2.10528e9, "algorithmic_per_launch": 72 * 16384 ** 2}},
-    "f16s_x4w": {"bytes_per_launch": 4 * (2.21023e9 + 1.56971e9), "kernel_hash": "b400427d9e6bdb2d",
-                 "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.21023e9,
-                         "dram_write_per_launch": 4 * 1.56971e9, "algorithmic_per_launch": 56 * 16384 ** 2}},
+    "f32_x4w": {"bytes_per_launch": 4 * (2.76140e9 + 2.10505e9), "kernel_hash": "195451d24ed7397c",
+                "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.76140e9,
+                        "dram_write_per_launch": 4 * 2.10505e9, "algorithmic_per_launch": 72 * 16384 ** 2}},
+    "f16s_x4w": {"bytes_per_launch": 4 * (2.20884e9 + 1.57010e9), "kernel_hash": "195451d24ed7397c",
+                 "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.20884e9,
+                         "dram_write_per_launch": 4 * 1.57010e9, "algorithmic_per_launch": 56 * 16384 ** 2}},
 }
 
 

@@ -958,6 +958,14 @@ __host__ __device__ constexpr bool wv_la2() {
 #ifndef LBM_WV_L1FIRST_F16S
 #define LBM_WV_L1FIRST_F16S 1
 #endif
+// FP32: step 1's load buffers and the delay lines of population 2 as
+// circular buffers of four, indexed by the iteration's phase in its group of
+// four (no register copies: 3.31 against 3.35 ms per four-step launch at
+// 16384^2 on GB300), or (0) two buffers whose pulls are copied before the
+// reload, and delay lines shifted every iteration
+#ifndef LBM_WV_CIRC
+#define LBM_WV_CIRC 1
+#endif
 template <int S>
 __host__ __device__ constexpr bool wv_l1first() {
     return S == S_F16S ? LBM_WV_L1FIRST_F16S != 0 : LBM_WV_L1FIRST_F32 != 0;
@@ -989,6 +997,7 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     constexpr int W = kWvW, R = kWvRow, OX = wv_ox<T>(), PL = kWvD * kWvRow, RP = kWvRP * PL, D = kWvD - 1;
     constexpr bool PA2 = wv_la2<S>();             // populations two rows ahead
     constexpr bool L1FIRST = wv_l1first<S>();     // step 1 collides before the other levels
+    constexpr bool CIRC = LBM_WV_CIRC != 0 && S == S_F32 && PA2 && !L1FIRST;
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
     const int xs = strip * OX - (T - 1) + t;      // lattice column of slot t (unwrapped)
@@ -1018,15 +1027,15 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     // iteration earlier) before the producer (level r + 1) of the same
     // iteration shifts the line; producers run in consecutive iterations, from
     // three iterations before their consumer's first to one before its last.
-    float v2[T - 1][3], v4[T - 1];
+    float v2[T - 1][4], v4[T - 1];
 #pragma unroll
-    for (int r = 0; r < T - 1; ++r) v2[r][0] = v2[r][1] = v2[r][2] = v4[r] = 0.0f;
+    for (int r = 0; r < T - 1; ++r) v2[r][0] = v2[r][1] = v2[r][2] = v2[r][3] = v4[r] = 0.0f;
     // Step 1's pulls (one row ahead, PA2: two) and the force (LA2: two rows
     // ahead, else one) in registers.  The row offsets of the next row to load
     // advance one row per load (rows are loaded in order), with the periodic
     // wrap.
     constexpr bool LA2 = S == S_F32 || PA2;
-    Pulled<S> q[PA2 ? 2 : 1];
+    Pulled<S> q[CIRC ? 4 : (PA2 ? 2 : 1)];
     float qg[LA2 ? 2 : 1][2];
     int ly = wrap_slot<false>(ybeg, ny);          // lattice row of the next population load
     I lr0 = (I)ly * nx, lrm = (I)wrap_dec(ly, ny) * nx, lrp = (I)wrap_inc(ly, ny) * nx;
@@ -1060,7 +1069,8 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     // the stores of level T are predicated.
     auto iter = [&](int i, auto full_c, auto buf_c) {
         constexpr bool FULL = decltype(full_c)::value;
-        constexpr int b = decltype(buf_c)::value;   // load buffers of local row i (i mod 2 with
+        constexpr int K = decltype(buf_c)::value;   // phase: i mod 4 (CIRC), else i mod 2
+        constexpr int b = LA2 ? (K & 1) : 0;        // load buffers of local row i (i mod 2 with
                                                     // two rows ahead, else 0)
         const bool l1 = FULL || i < n1;
 #pragma unroll
@@ -1087,12 +1097,18 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
             t4 = fs[3];
         };
         if (l1) {
-            constexpr int bq = PA2 ? b : 0;
-            pull_decode<S>(a, q[bq], f1, c.theta);
-            // L1FIRST: collide row i before reloading its buffers (ring slot i
-            // mod 4 is not among the slots the levels below read)
-            if constexpr (L1FIRST) level1();
-            if (FULL || i + (PA2 ? 2 : 1) < n1) load1(bq);
+            if constexpr (CIRC) {
+                // row i + 2 into the buffer row i - 2 left; row i stays in
+                // buffer K until step 1 collides it below
+                if (FULL || i + 2 < n1) load1((K + 2) & 3);
+            } else {
+                constexpr int bq = PA2 ? b : 0;
+                pull_decode<S>(a, q[bq], f1, c.theta);
+                // L1FIRST: collide row i before reloading its buffers (ring slot i
+                // mod 4 is not among the slots the levels below read)
+                if constexpr (L1FIRST) level1();
+                if (FULL || i + (PA2 ? 2 : 1) < n1) load1(bq);
+            }
             if (FULL || i + (LA2 ? 2 : 1) < n1) load_force(b);
         }
         // Levels T..2: local row j = i - 2(tau - 1), pulled from ring tau - 1.
@@ -1105,7 +1121,7 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
             const int rm = ((j - 1) & D) * R, r0 = (j & D) * R, rp = ((j + 1) & D) * R;
             float f[8];
             f[0] = sp[0 * PL + r0 - 1];          // f_p(x) = f*_p(x - c_p)
-            f[1] = v2[tau - 2][2];
+            f[1] = CIRC ? v2[tau - 2][(K + 1) & 3] : v2[tau - 2][2];   // made 3 iterations ago
             f[2] = sp[1 * PL + r0 + 1];
             f[3] = v4[tau - 2];
             f[4] = sp[2 * PL + rm - 1];
@@ -1124,9 +1140,13 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
                 d[3 * PL] = fs[5];
                 d[4 * PL] = fs[6];
                 d[5 * PL] = fs[7];
-                v2[tau - 1][2] = v2[tau - 1][1];
-                v2[tau - 1][1] = v2[tau - 1][0];
-                v2[tau - 1][0] = fs[1];
+                if constexpr (CIRC) {
+                    v2[tau - 1][K] = fs[1];
+                } else {
+                    v2[tau - 1][2] = v2[tau - 1][1];
+                    v2[tau - 1][1] = v2[tau - 1][0];
+                    v2[tau - 1][0] = fs[1];
+                }
                 v4[tau - 1] = fs[3];
             } else {
                 // every thread collides; only the stores are predicated
@@ -1143,10 +1163,16 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
             }
         }
         if (l1) {
-            if constexpr (!L1FIRST) level1();
-            v2[0][2] = v2[0][1];
-            v2[0][1] = v2[0][0];
-            v2[0][0] = t2;
+            if constexpr (CIRC) {
+                pull_decode<S>(a, q[K], f1, c.theta);
+                level1();
+                v2[0][K] = t2;
+            } else {
+                if constexpr (!L1FIRST) level1();
+                v2[0][2] = v2[0][1];
+                v2[0][1] = v2[0][0];
+                v2[0][0] = t2;
+            }
             v4[0] = t4;
         }
         __syncthreads();
@@ -1162,10 +1188,21 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
     if (CHECK && store_ok) snap_next(fb);         // level T's first row is y0
     const int m0 = (fb + 3) >> 2, m1 = (fe + 1) >> 2;   // groups i = 4m .. 4m + 3 within [fb, fe]
     using B0 = std::integral_constant<int, 0>;
-    using B1 = std::integral_constant<int, LA2 ? 1 : 0>;
+    using B1 = std::integral_constant<int, 1>;
+    using B2 = std::integral_constant<int, CIRC ? 2 : 0>;
+    using B3 = std::integral_constant<int, CIRC ? 3 : 1>;
     auto iter_any = [&](int i) {
-        if (LA2 && (i & 1)) iter(i, std::false_type{}, B1{});
-        else iter(i, std::false_type{}, B0{});
+        if constexpr (CIRC) {
+            switch (i & 3) {
+                case 0: iter(i, std::false_type{}, B0{}); break;
+                case 1: iter(i, std::false_type{}, B1{}); break;
+                case 2: iter(i, std::false_type{}, B2{}); break;
+                default: iter(i, std::false_type{}, B3{}); break;
+            }
+        } else {
+            if (LA2 && (i & 1)) iter(i, std::false_type{}, B1{});
+            else iter(i, std::false_type{}, B0{});
+        }
     };
     int i = 0;
     if (m1 > m0) {
@@ -1174,8 +1211,8 @@ __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float
             const int ib = m << 2;
             iter(ib, std::true_type{}, B0{});
             iter(ib + 1, std::true_type{}, B1{});
-            iter(ib + 2, std::true_type{}, B0{});
-            iter(ib + 3, std::true_type{}, B1{});
+            iter(ib + 2, std::true_type{}, B2{});
+            iter(ib + 3, std::true_type{}, B3{});
         }
         i = 4 * m1;
     }
