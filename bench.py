@@ -61,12 +61,12 @@ FP64_PEAK_GINST = 625.0
 # per output column) and segment length as the 16384^2 launch, so a launch's
 # traffic is 4x the capture's (nodes x4).  Mean of three launches.
 NCU_TRAFFIC = {
-    "f32_x4w": {"bytes_per_launch": 4 * (2.76140e9 + 2.10505e9), "kernel_hash": "195451d24ed7397c",
-                "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.76140e9,
-                        "dram_write_per_launch": 4 * 2.10505e9, "algorithmic_per_launch": 72 * 16384 ** 2}},
-    "f16s_x4w": {"bytes_per_launch": 4 * (2.20884e9 + 1.57010e9), "kernel_hash": "195451d24ed7397c",
-                 "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.20884e9,
-                         "dram_write_per_launch": 4 * 1.57010e9, "algorithmic_per_launch": 56 * 16384 ** 2}},
+    "f32_x4w": {"bytes_per_launch": 4 * (2.76050e9 + 2.10493e9), "kernel_hash": "fb0329a445f0d126",
+                "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.76050e9,
+                        "dram_write_per_launch": 4 * 2.10493e9, "algorithmic_per_launch": 72 * 16384 ** 2}},
+    "f16s_x4w": {"bytes_per_launch": 4 * (2.20988e9 + 1.57011e9), "kernel_hash": "fb0329a445f0d126",
+                 "ncu": {"case": "8192^2, 256-row segments, x4", "dram_read_per_launch": 4 * 2.20988e9,
+                         "dram_write_per_launch": 4 * 1.57011e9, "algorithmic_per_launch": 56 * 16384 ** 2}},
 }
 
 

@@ -990,14 +990,17 @@ template <int S, int T> constexpr int wv_minb() {
 // y0 + rows - 1, T steps; wv_ring is the block's (T-1) rings.  With CHECK the thread's residual partials of
 // level T are accumulated into acc.  Called by k_wave (one block per strip
 // and segment) and by the batched arena (one call per work item).
-template <int S, bool GEN, int T, bool CHECK, typename I>
+template <int S, bool GEN, int T, bool CHECK, typename I, bool CIRC_OK = false>
 __device__ __forceinline__ void wave_block(const StepParams& a, const Coef<float>& c, float* wv_ring,
                                            int strip, int y0, int rows, ResAcc<S>& acc) {
     static_assert(T >= 2 && T <= 4, "two to four steps per launch");
     constexpr int W = kWvW, R = kWvRow, OX = wv_ox<T>(), PL = kWvD * kWvRow, RP = kWvRP * PL, D = kWvD - 1;
     constexpr bool PA2 = wv_la2<S>();             // populations two rows ahead
     constexpr bool L1FIRST = wv_l1first<S>();     // step 1 collides before the other levels
-    constexpr bool CIRC = LBM_WV_CIRC != 0 && S == S_F32 && PA2 && !L1FIRST;
+    // (CIRC_OK: the single-lattice kernel; the batched arena's kernel, which also
+    // holds the two-step tiles, spills more with the larger code and keeps the
+    // copies: config 4 measured 141 against 165 GLUPS with them)
+    constexpr bool CIRC = CIRC_OK && LBM_WV_CIRC != 0 && S == S_F32 && PA2 && !L1FIRST;
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
     const int xs = strip * OX - (T - 1) + t;      // lattice column of slot t (unwrapped)
@@ -1227,7 +1230,7 @@ k_wave(const StepParams a, const Coef<float> c, int seg) {
     const int strip = (int)(blockIdx.x % (unsigned)nstrips);
     const int y0 = (int)(blockIdx.x / (unsigned)nstrips) * seg;
     ResAcc<S> acc;
-    wave_block<S, GEN, T, CHECK, I>(a, c, wv_ring, strip, y0, min(seg, a.ny - y0), acc);
+    wave_block<S, GEN, T, CHECK, I, true>(a, c, wv_ring, strip, y0, min(seg, a.ny - y0), acc);
     if (CHECK) residual_reduce<S>(a, acc);
 }
 
