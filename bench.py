@@ -785,7 +785,7 @@ def run_jitter(args, P):
 
 
 def run_batched(args, P):
-    """Config-4 stream (2048 problems, sides log-uniform in [32, 1024], nu in
+    """Batched stream (2048 problems, sides log-uniform in [32, 1024], nu in
     [0, 0.45], 8 random force modes, FP32, tol 1e-8): the problems whose longer
     side is at most --batched-cap, solved once in one arena and once one at a
     time through lbm_solve.  Both through the public API, host in and out."""
@@ -809,7 +809,7 @@ def run_batched(args, P):
         st, it = plain_solve(P, p, args.tol, args.check_every)
         iters += it
     tp = time.perf_counter() - t0
-    return {"workload": "config-4 stream (seed %#x), %d problems with max side <= %d, FP32, "
+    return {"workload": "batched stream of independent problems (seed %#x), %d problems with max side <= %d, FP32, "
                         "tol %g, residual every %d steps" % (0x5EED_BA7C4ED, len(probs),
                                                              args.batched_cap, args.tol,
                                                              args.check_every),
@@ -825,7 +825,7 @@ def run_batched(args, P):
 
 
 def run_served(args, P):
-    """Config-5 stream (Poisson arrivals, sides log-uniform in [64, 4096], nu in
+    """Served stream (Poisson arrivals, sides log-uniform in [64, 4096], nu in
     [0, 0.45], 8 random force modes, tol 1e-8, FP32 or FP16-shifted per request,
     HBM budget 150 GB): the first --served-max requests with max side <= --served-cap,
     arriving at --served-rate requests/s, through lbm_server_*; compared with a
@@ -872,7 +872,7 @@ def run_served(args, P):
         done = max(done, arr) + s
         lat.append((done - arr) * 1e3)
     lat = np.array(lat)
-    return {"workload": "config-5 stream (seed %#x): first %d requests with max side <= %d, "
+    return {"workload": "served stream of solve requests (seed %#x): first %d requests with max side <= %d, "
                         "Poisson arrivals at %g req/s, tol %g, FP32/FP16S per request, "
                         "HBM budget %g GB (each storage type's arena half of it)" % (
                             0x5E4FED, len(reqs), args.served_cap, args.served_rate, args.tol,
